@@ -1,0 +1,155 @@
+"""Seeded, synthetic initial data for the test problems of Pan & Xu
+(arXiv 1909.01580, Sec. 4) and the benchmark workloads.
+
+This module only evaluates initial conditions; it holds none of the
+scheme's arithmetic, so both the CUDA path and the oracle can take their
+inputs from it.  Every state is returned as conservative cell averages
+(rho, rho U, rho V, rho W, rho E) in SoA layout [5][nz][ny][nx], FP64.
+
+Reading (cell averages versus point values): initial data are cell
+averages.  The advection data are averaged exactly (the profile is a plane
+sine wave); the Taylor-Green data are averaged with a 4-point Gauss-Legendre
+rule per axis applied to the conservative variables; piecewise-constant
+octant data are exact when the octant planes fall on cell faces.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class Box:
+    n: tuple
+    lo: tuple
+    hi: tuple
+
+    @property
+    def h(self):
+        return tuple((self.hi[d] - self.lo[d]) / self.n[d] for d in range(3))
+
+    def centres(self):
+        """cell-centre coordinate arrays, each of shape [nz][ny][nx]"""
+        ax = [self.lo[d] + (np.arange(self.n[d]) + 0.5) * self.h[d] for d in range(3)]
+        z, y, x = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+        return x, y, z
+
+
+def _conservative(rho, u, v, w, p, gamma):
+    E = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v + w * w)
+    return np.stack([rho, rho * u, rho * v, rho * w, E]).astype(np.float64)
+
+
+def density_advection(n, t=0.0, gamma=1.4, lo=(0.0, 0.0, 0.0), hi=(2.0, 2.0, 2.0), amp=0.2):
+    """3D density advection (Sec. 4 accuracy test): rho = 1 + 0.2 sin(pi(x+y+z-t)),
+    U = V = W = 1, p = 1 on [0,2]^3, periodic.  Exact cell averages at time t."""
+    box = Box(tuple(n), tuple(lo), tuple(hi))
+    x, y, z = box.centres()
+    fac = 1.0
+    for d in range(3):
+        a = 0.5 * math.pi * box.h[d]
+        fac *= math.sin(a) / a
+    rho = 1.0 + amp * np.sin(math.pi * (x + y + z - 3.0 * t)) * fac
+    one = np.ones_like(rho)
+    # all conservative variables are affine in rho, so averaging is exact
+    return _conservative(rho, one, one, one, one, gamma)
+
+
+def _gauss4():
+    g, w = np.polynomial.legendre.leggauss(4)
+    return 0.5 * g, 0.5 * w  # on [-1/2, 1/2], weights sum to 1
+
+
+def cell_average(box: Box, fn, gamma=1.4):
+    """4-point Gauss-Legendre per axis average of the conservative variables
+    returned by fn(x, y, z) -> (rho, u, v, w, p)."""
+    g, w = _gauss4()
+    x, y, z = box.centres()
+    acc = np.zeros((5,) + x.shape)
+    h = box.h
+    for a in range(4):
+        for b in range(4):
+            for c in range(4):
+                prims = fn(x + g[a] * h[0], y + g[b] * h[1], z + g[c] * h[2])
+                acc += w[a] * w[b] * w[c] * _conservative(*prims, gamma)
+    return acc
+
+
+def taylor_green(n, mach=0.1, gamma=1.4, L=1.0, V0=1.0, rho0=1.0):
+    """Taylor-Green vortex on [-pi L, pi L]^3 (Sec. 4): u = V0 sin x cos y cos z,
+    v = -V0 cos x sin y cos z, w = 0, p = p0 + rho0 V0^2/16 (cos 2x + cos 2y)(cos 2z + 2).
+    Reading of "uniform temperature": rho = rho0 p/p0 with p0 = rho0 V0^2/(gamma M0^2)."""
+    lo = (-math.pi * L,) * 3
+    hi = (math.pi * L,) * 3
+    p0 = rho0 * V0 * V0 / (gamma * mach * mach)
+    box = Box(tuple(n), lo, hi)
+
+    def fn(x, y, z):
+        u = V0 * np.sin(x / L) * np.cos(y / L) * np.cos(z / L)
+        v = -V0 * np.cos(x / L) * np.sin(y / L) * np.cos(z / L)
+        w = np.zeros_like(u)
+        p = p0 + rho0 * V0 * V0 / 16.0 * (np.cos(2 * x / L) + np.cos(2 * y / L)) * (np.cos(2 * z / L) + 2.0)
+        rho = rho0 * p / p0
+        return rho, u, v, w, p
+
+    return cell_average(box, fn, gamma), lo, hi
+
+
+def octant_riemann(n, seed=0, gamma=1.4):
+    """3D octant Riemann problem on [0,1]^3: eight constant states, one per
+    octant, rho, p ~ U[0.1, 1.5], velocity direction uniform on the sphere
+    with magnitude U[0, 1] (seeded).  Exact averages for even n."""
+    rng = np.random.default_rng(seed)
+    rho_o = rng.uniform(0.1, 1.5, 8)
+    p_o = rng.uniform(0.1, 1.5, 8)
+    dirs = rng.normal(size=(8, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    vel = dirs * rng.uniform(0.0, 1.0, (8, 1))
+    box = Box(tuple(n), (0.0,) * 3, (1.0,) * 3)
+    x, y, z = box.centres()
+    o = (x > 0.5).astype(int) + 2 * (y > 0.5).astype(int) + 4 * (z > 0.5).astype(int)
+    return _conservative(rho_o[o], vel[o, 0], vel[o, 1], vel[o, 2], p_o[o], gamma)
+
+
+def uniform_flow(n, rho=1.0, u=(1.0, 1.0, 1.0), p=1.0, gamma=1.4):
+    """Uniform free stream (Sec. 4 geometric conservation test)."""
+    shape = (n[2], n[1], n[0])
+    one = np.ones(shape)
+    return _conservative(rho * one, u[0] * one, u[1] * one, u[2] * one, p * one, gamma)
+
+
+def smooth_random(n, seed=0, gamma=1.4, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), amp=0.1, modes=3):
+    """Seeded smooth periodic state: a few random Fourier modes on each
+    primitive variable around rho = 1, p = 1, |U| ~ 0.3 (point values at
+    cell centres, taken as cell averages)."""
+    rng = np.random.default_rng(seed)
+    box = Box(tuple(n), tuple(lo), tuple(hi))
+    x, y, z = box.centres()
+    L = [hi[d] - lo[d] for d in range(3)]
+
+    def field(base, a):
+        f = np.full(x.shape, base, dtype=np.float64)
+        for _ in range(modes):
+            k = rng.integers(-2, 3, 3)
+            ph = rng.uniform(0, 2 * math.pi)
+            c = rng.uniform(-a, a)
+            f += c * np.sin(2 * math.pi * (k[0] * (x - lo[0]) / L[0] + k[1] * (y - lo[1]) / L[1]
+                                           + k[2] * (z - lo[2]) / L[2]) + ph)
+        return f
+
+    rho = field(1.0, amp)
+    u = field(0.3, amp)
+    v = field(-0.2, amp)
+    w = field(0.1, amp)
+    p = field(1.0, amp)
+    return _conservative(rho, u, v, w, p, gamma)
+
+
+def primitive(q, gamma=1.4):
+    """(rho, u, v, w, p) of a conservative state array."""
+    rho = q[0]
+    u, v, w = q[1] / rho, q[2] / rho, q[3] / rho
+    p = (gamma - 1.0) * (q[4] - 0.5 * rho * (u * u + v * v + w * w))
+    return rho, u, v, w, p
