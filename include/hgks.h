@@ -1,0 +1,165 @@
+/*
+ * hgks.h -- C ABI of the GB300 (sm_103a) implementation of the high-order
+ * gas-kinetic scheme with third-order 3D WENO-AO reconstruction of Pan & Xu,
+ * "High-order gas-kinetic scheme with three-dimensional WENO reconstruction
+ * for the Euler and Navier-Stokes solutions" (arXiv 1909.01580).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an int status (HGKS_OK or a negative HGKS_E_* code);
+ *     nothing crosses the ABI as an exception.  hgks_last_error() gives a
+ *     one-line reason for the last failure on a handle.
+ *   - A handle owns all of its device memory; the caller owns every host
+ *     buffer it passes.  Buffers flagged on_device = 1 are device pointers
+ *     on the handle's device, valid in stream order on the handle's stream.
+ *   - State arrays are conservative cell averages (rho, rho U, rho V, rho W,
+ *     rho E) in SoA layout [5][nz][ny][nx], x fastest, FP64.
+ *   - Calls are ordered on the handle's stream.  Calls that return host
+ *     data or a status synchronise that stream before returning.
+ *   - There is no CPU fallback: without a usable CUDA device hgks_create
+ *     fails with HGKS_E_CUDA.
+ */
+#ifndef HGKS_H
+#define HGKS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hgks hgks_t;
+
+/* Mesh and arithmetic of a solver instance. */
+typedef struct {
+    int n[3];          /* cells in x, y, z (x fastest in memory)                    */
+    double lo[3];      /* physical box [lo, hi]                                     */
+    double hi[3];
+    int mesh;          /* 0: uniform mesh of cubic cells (Sec. 4 accuracy, TGV and
+                          Riemann tests); other values are rejected                 */
+    double mesh_amp;   /* reserved for mapped meshes; must be 0                     */
+    double mesh_omega; /* reserved for mapped meshes; must be 0                     */
+    int precision;     /* HGKS_FP64 or HGKS_MIXED                                   */
+} hgks_grid_t;
+
+enum { HGKS_FP64 = 0,   /* every operation in FP64                               */
+       HGKS_MIXED = 1   /* reconstruction and Gauss-point flux in FP32; face-flux
+                           accumulation and the two-stage update in FP64         */
+};
+
+enum { HGKS_BC_PERIODIC = 0, HGKS_BC_REFLECTIVE = 1 };
+
+enum {
+    HGKS_OK = 0,
+    HGKS_E_INVALID = -1,     /* bad argument                                     */
+    HGKS_E_NOMEM = -2,       /* device allocation failed                         */
+    HGKS_E_CUDA = -3,        /* CUDA runtime error                               */
+    HGKS_E_NONPHYSICAL = -4, /* NaN or non-positive density/pressure after a step */
+    HGKS_E_TIMEOUT = -5,     /* a bounded device wait gave up                    */
+    HGKS_E_STATE = -6        /* call out of order (e.g. step before set_state)   */
+};
+
+/* Create a solver on the current CUDA device.
+ *   grid    mesh and precision (see hgks_grid_t); cells must be cubes and
+ *           every axis needs at least 2 cells.
+ *   gamma   ratio of specific heats; K = (5 - 3 gamma)/(gamma - 1) internal
+ *           degrees of freedom of the Maxwellian (Sec. 3, BGK model).
+ *   mu      dynamic viscosity.  mu = 0 selects the inviscid collision time
+ *           tau = eps dt + C |p_l - p_r|/(p_l + p_r) dt, mu > 0 the viscous one
+ *           tau = mu/p + C |p_l - p_r|/(p_l + p_r) dt (Sec. 4).
+ *   Pr      Prandtl number; when mu > 0 and Pr != 1 the energy flux takes the
+ *           heat-flux correction F_E += (1/Pr - 1) q (the paper is silent on
+ *           Pr; this is the usual BGK correction).
+ *   bc      per face -x,+x,-y,+y,-z,+z: HGKS_BC_PERIODIC (must pair) or
+ *           HGKS_BC_REFLECTIVE (mirror, normal momentum negated).
+ *   stream  cudaStream_t to order all work on, or NULL for a private stream.
+ *   out     receives the handle.
+ * Paper constants are defaults: Gamma = 0.0025 (gamma_0 = 0.94), epsilon
+ * = 1e-8 in the nonlinear weights, tau constants eps = 0.01, C = 1;
+ * hgks_set_option changes them. */
+int hgks_create(const hgks_grid_t *grid, double gamma, double mu, double Pr, const int bc[6], void *stream,
+                hgks_t **out);
+
+/* Change a scheme constant: "Gamma" (linear weight of each of the 24
+ * sub-stencils, Sec. 2), "weno_eps", "weno_pow" (1 or 2, exponent of
+ * tau/(beta + eps) in eq. nonlinear), "tau_eps", "tau_C" (collision time,
+ * Sec. 4), "limiter" (1/0: positivity fallback of Sec. 4). */
+int hgks_set_option(hgks_t *h, const char *key, double value);
+
+/* Load the state q ([5][nz][ny][nx] FP64, copied) at time t. */
+int hgks_set_state(hgks_t *h, const double *q, int on_device, double t);
+
+/* Copy the state out into q ([5][nz][ny][nx] FP64) and the time into *t
+ * (t may be NULL). */
+int hgks_get_state(hgks_t *h, double *q, int on_device, double *t);
+
+/* Advance nsteps two-stage fourth-order steps (Sec. 3):
+ *   Q*      = Q^n + dt/2 L(Q^n) + dt^2/8 dL/dt(Q^n)
+ *   Q^{n+1} = Q^n + dt L(Q^n) + dt^2/6 (dL/dt(Q^n) + 2 dL/dt(Q*)).
+ * dt_fixed > 0 fixes dt; otherwise dt = cfl * min_cells h/(|U| + c),
+ * reduced on the device and clipped so that t does not pass t_end; steps
+ * after t reaches t_end do nothing.  *t_out and *steps_done (either may be
+ * NULL) receive the time reached and the steps taken; passing them
+ * synchronises the stream.  Returns HGKS_E_NONPHYSICAL if a step produced
+ * NaN or non-positive density or pressure. */
+int hgks_step(hgks_t *h, int nsteps, double cfl, double dt_fixed, double t_end, double *t_out, int *steps_done);
+
+/* The finite-volume operator L(Q) = -1/|Omega| sum_faces F.n (eq. finite)
+ * and its time derivative dL/dt(Q) for the resident state with time step
+ * dt (which enters the flux through the collision time and the two time
+ * levels dt, dt/2 of eq. expansion-1).  L and dLdt: [5][nz][ny][nx] FP64. */
+int hgks_flux(hgks_t *h, double dt, double *L, double *dLdt, int on_device);
+
+/* The reconstructed polynomial of every interior cell (Sec. 2): coef
+ * [ncell][5][9] FP64 (always FP64 on output) holds the coefficients of
+ * P~ = Q_c + sum_n c_n p_n in the scaled coordinates X = (x - x_c)/h, with
+ * p_n = (X, Y, Z, X^2 - 1/12, Y^2 - 1/12, Z^2 - 1/12, XY, XZ, YZ); flag
+ * [ncell] int (may be NULL) is 1 where the positivity fallback set P~ = Q_c.
+ * Host buffers. */
+int hgks_reconstruct(hgks_t *h, double *coef, int *flag);
+
+/* Gas-kinetic flux at n Gauss points (Sec. 3, eq. flux with the time
+ * integrals of eq. expansion-1), a test surface for the flux kernel.
+ *   in     [n][40] FP64 host, local frame (n_x, n_y, n_z), n_x from the left
+ *          to the right cell: W_l, dW_l/dn_x, dW_l/dn_y, dW_l/dn_z, W_r,
+ *          dW_r/dn_x, dW_r/dn_y, dW_r/dn_z (5 values each).
+ *   ug     [n][3] grid velocity in the local frame, or NULL for a fixed mesh.
+ *   dt     time step.
+ *   params gamma, mu, Pr, tau_eps, tau_C.
+ *   precision HGKS_FP64 or HGKS_MIXED (FP32 arithmetic).
+ *   F, dF  [n][5] FP64 host outputs: flux per unit area and its time
+ *          derivative in the local frame. */
+int hgks_point_flux(int n, const double *in, const double *ug, double dt, const double params[5], int precision,
+                    double *F, double *dF);
+
+/* Phases of a stage, for hgks_get_timing. */
+enum { HGKS_PHASE_HALO = 0,   /* ghost fill                                 */
+       HGKS_PHASE_RECON = 1,  /* WENO-AO reconstruction (Sec. 2)            */
+       HGKS_PHASE_FLUX = 2,   /* Gauss-point gas-kinetic face flux (Sec. 3) */
+       HGKS_PHASE_UPDATE = 3, /* two-stage update (Sec. 3)                  */
+       HGKS_PHASE_CFL = 4,    /* CFL reduction and dt                        */
+       HGKS_NPHASE = 5 };
+
+/* Turn per-phase timing on (1) or off (0) and reset the accumulators.  While
+ * on, each launch group of a phase is bracketed by CUDA events recorded on
+ * the handle's stream.  Synchronises the stream. */
+int hgks_set_timing(hgks_t *h, int enable);
+
+/* Device time (ms, CUDA events) and kernel launches accumulated per phase
+ * since the last hgks_set_timing.  ms and launches: [HGKS_NPHASE] host
+ * arrays.  Synchronises the stream. */
+int hgks_get_timing(hgks_t *h, double ms[HGKS_NPHASE], unsigned long long launches[HGKS_NPHASE]);
+
+/* Kernel launches this handle has issued since creation (for accounting). */
+unsigned long long hgks_launch_count(const hgks_t *h);
+
+/* Bytes of device memory this handle holds. */
+unsigned long long hgks_device_bytes(const hgks_t *h);
+
+/* One-line reason for the last failure on h (or on creation when h is NULL). */
+const char *hgks_last_error(const hgks_t *h);
+
+/* Free the handle and its device memory. */
+void hgks_destroy(hgks_t *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

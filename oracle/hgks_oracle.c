@@ -256,7 +256,6 @@ typedef struct {
     orc_dims D;
     double *vx;        /* [nvert][3] vertex positions   */
     double *vv;        /* [nvert][3] vertex velocities  */
-    cell_geom *cg;     /* [ncell]                       */
 } orc_geom;
 
 static void cell_vertices(const orc_geom *G, int i, int j, int k, double hv[2][2][2][3])
@@ -268,50 +267,50 @@ static void cell_vertices(const orc_geom *G, int i, int j, int k, double hv[2][2
                     hv[a][b][c][d] = G->vx[vid(&G->D, i + a, j + b, k + c) * 3 + d];
 }
 
+/* volume, centroid and quadrature points of cell (i,j,k) by the 2x2x2
+ * Gauss rule on its trilinear map (Sec. 2) */
+static void cell_geometry(const orc_geom *G, int i, int j, int k, cell_geom *cg)
+{
+    double hv[2][2][2][3];
+    cell_vertices(G, i, j, k, hv);
+    double vol = 0.0, m1[3] = {0, 0, 0};
+    int q = 0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int cc = 0; cc < 2; ++cc, ++q) {
+                double p[3] = {GNODE[a], GNODE[b], GNODE[cc]}, X[3], J[3][3];
+                trilinear(hv, p, X, J);
+                double w = 0.125 * fabs(det3(J));
+                cg->qw[q] = w;
+                for (int d = 0; d < 3; ++d) cg->qx[q][d] = X[d];
+                vol += w;
+                for (int d = 0; d < 3; ++d) m1[d] += w * X[d];
+            }
+    cg->vol = vol;
+    for (int d = 0; d < 3; ++d) cg->cen[d] = m1[d] / vol;
+    cg->h = cbrt(vol);
+}
+
 static int geom_build(const orc_cfg *c, double t, orc_geom *G)
 {
     G->D = make_dims(c);
     const orc_dims *D = &G->D;
     G->vx = (double *)malloc(D->nvert * 3 * sizeof(double));
     G->vv = (double *)malloc(D->nvert * 3 * sizeof(double));
-    G->cg = (cell_geom *)malloc(D->ncell * sizeof(cell_geom));
-    if (!G->vx || !G->vv || !G->cg) return -1;
+    if (!G->vx || !G->vv) return -1;
     for (int k = -GH; k <= c->n[2] + GH; ++k)
         for (int j = -GH; j <= c->n[1] + GH; ++j)
             for (int i = -GH; i <= c->n[0] + GH; ++i) {
                 size_t v = vid(D, i, j, k);
                 mesh_vertex(c, i, j, k, t, &G->vx[v * 3], &G->vv[v * 3]);
             }
-    for (int k = -GH; k < c->n[2] + GH; ++k)
-        for (int j = -GH; j < c->n[1] + GH; ++j)
-            for (int i = -GH; i < c->n[0] + GH; ++i) {
-                cell_geom *cg = &G->cg[cid(D, i, j, k)];
-                double hv[2][2][2][3];
-                cell_vertices(G, i, j, k, hv);
-                double vol = 0.0, m1[3] = {0, 0, 0};
-                int q = 0;
-                for (int a = 0; a < 2; ++a)
-                    for (int b = 0; b < 2; ++b)
-                        for (int cc = 0; cc < 2; ++cc, ++q) {
-                            double p[3] = {GNODE[a], GNODE[b], GNODE[cc]}, X[3], J[3][3];
-                            trilinear(hv, p, X, J);
-                            double w = 0.125 * fabs(det3(J));
-                            cg->qw[q] = w;
-                            for (int d = 0; d < 3; ++d) cg->qx[q][d] = X[d];
-                            vol += w;
-                            for (int d = 0; d < 3; ++d) m1[d] += w * X[d];
-                        }
-                cg->vol = vol;
-                for (int d = 0; d < 3; ++d) cg->cen[d] = m1[d] / vol;
-                cg->h = cbrt(vol);
-            }
     return 0;
 }
 
 static void geom_free(orc_geom *G)
 {
-    free(G->vx); free(G->vv); free(G->cg);
-    G->vx = G->vv = NULL; G->cg = NULL;
+    free(G->vx); free(G->vv);
+    G->vx = G->vv = NULL;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -483,7 +482,14 @@ static double poly_value(const cell_rec *r, const double *coef, double qc, int n
 static void reconstruct_cell(const orc_cfg *c, const orc_geom *G, const double *Qp, int i, int j, int k, cell_rec *r)
 {
     const orc_dims *D = &G->D;
-    const cell_geom *gc = &G->cg[cid(D, i, j, k)];
+    /* geometry of the 3x3x3 block around the cell (corners unused) */
+    cell_geom blk[3][3][3];
+    for (int c2 = -1; c2 <= 1; ++c2)
+        for (int b2 = -1; b2 <= 1; ++b2)
+            for (int a2 = -1; a2 <= 1; ++a2)
+                if (a2 * b2 * c2 == 0) cell_geometry(G, i + a2, j + b2, k + c2, &blk[c2 + 1][b2 + 1][a2 + 1]);
+#define BLK(o0, o1, o2) (&blk[(o2) + 1][(o1) + 1][(o0) + 1])
+    const cell_geom *gc = BLK(0, 0, 0);
     for (int d = 0; d < 3; ++d) r->cen[d] = gc->cen[d];
     r->h = gc->h;
     cell_monomial_means(gc, r->cen, r->h, r->mean);
@@ -497,7 +503,7 @@ static void reconstruct_cell(const orc_cfg *c, const orc_geom *G, const double *
     for (int s = 0; s < ns; ++s) {
         int ii = i + off[s][0], jj = j + off[s][1], kk = k + off[s][2];
         double mn[9];
-        cell_monomial_means(&G->cg[cid(D, ii, jj, kk)], r->cen, r->h, mn);
+        cell_monomial_means(BLK(off[s][0], off[s][1], off[s][2]), r->cen, r->h, mn);
         for (int m = 0; m < 9; ++m) A[s * 9 + m] = mn[m] - r->mean[m];
         for (int v = 0; v < NV; ++v) B[s * NV + v] = Qp[(size_t)v * D->ncell + cid(D, ii, jj, kk)] - r->Qc[v];
     }
@@ -513,7 +519,7 @@ static void reconstruct_cell(const orc_cfg *c, const orc_geom *G, const double *
         for (int rr = 0; rr < 4; ++rr) {
             int ii = i + so[s][rr][0], jj = j + so[s][rr][1], kk = k + so[s][rr][2];
             double mn[9];
-            cell_monomial_means(&G->cg[cid(D, ii, jj, kk)], r->cen, r->h, mn);
+            cell_monomial_means(BLK(so[s][rr][0], so[s][rr][1], so[s][rr][2]), r->cen, r->h, mn);
             for (int m = 0; m < 3; ++m) As[rr * 3 + m] = mn[m] - r->mean[m];
             for (int v = 0; v < NV; ++v) Bs[rr * NV + v] = Qp[(size_t)v * D->ncell + cid(D, ii, jj, kk)] - r->Qc[v];
         }
@@ -596,10 +602,30 @@ static void reconstruct_cell(const orc_cfg *c, const orc_geom *G, const double *
             for (int v = 0; v < NV; ++v)
                 for (int m = 0; m < 9; ++m) r->coef[v][m] = 0.0;
     }
+#undef BLK
+}
+
+/* what the flux needs of a reconstructed cell */
+typedef struct {
+    double cen[3], h;
+    double mean[9];
+    double Qc[NV];
+    double coef[NV][9];
+    int flag;
+} slim_rec;
+
+static void slim_from(const cell_rec *r, slim_rec *o)
+{
+    for (int d = 0; d < 3; ++d) o->cen[d] = r->cen[d];
+    o->h = r->h;
+    memcpy(o->mean, r->mean, sizeof o->mean);
+    memcpy(o->Qc, r->Qc, sizeof o->Qc);
+    memcpy(o->coef, r->coef, sizeof o->coef);
+    o->flag = r->flag;
 }
 
 /* value and physical gradient of P~ at x */
-static void rec_eval(const cell_rec *r, const double *x, double W[NV], double dW[NV][3])
+static void rec_eval(const slim_rec *r, const double *x, double W[NV], double dW[NV][3])
 {
     double X[3];
     for (int d = 0; d < 3; ++d) X[d] = (x[d] - r->cen[d]) / r->h;
@@ -1083,7 +1109,7 @@ static int inv3(const double *R, double *Ri)
 
 /* face flux integrated over the face (eq. flux-x), both time levels, in
  * the global frame, for the face whose left cell is (i,j,k)-e_d */
-static int face_flux(const orc_cfg *c, const orc_geom *G, const cell_rec *rl, const cell_rec *rr,
+static int face_flux(const orc_cfg *c, const orc_geom *G, const slim_rec *rl, const slim_rec *rr,
                      int d, int i, int j, int k, double dt, double *FF, double *dFF)
 {
     double fv[2][2][3], fu[2][2][3];
@@ -1209,9 +1235,10 @@ static int residuals(const orc_cfg *c, const orc_geom *G, const double *q, doubl
     const orc_dims *D = &G->D;
     size_t nint = (size_t)c->n[0] * c->n[1] * c->n[2];
     double *Qp = (double *)malloc(D->ncell * NV * sizeof(double));
-    cell_rec *rec = (cell_rec *)malloc(D->ncell * sizeof(cell_rec));
+    long *slot = (long *)malloc(D->ncell * sizeof(long));
     unsigned char *need = (unsigned char *)calloc(D->ncell, 1);
-    if (!Qp || !rec || !need) { free(Qp); free(rec); free(need); return -1; }
+    slim_rec *rec = NULL;
+    if (!Qp || !slot || !need) { free(Qp); free(slot); free(need); return -1; }
     fill_ghosts(c, D, q, Qp);
 
     /* which cells must be reconstructed: a requested cell and its 6 face neighbours */
@@ -1229,12 +1256,19 @@ static int residuals(const orc_cfg *c, const orc_geom *G, const double *q, doubl
     }
     int err = 0;
     int nx1 = c->n[0] + 2, ny1 = c->n[1] + 2, nz1 = c->n[2] + 2;
-    long nrec = (long)nx1 * ny1 * nz1;
+    long nrec = (long)nx1 * ny1 * nz1, nslot = 0;
+    for (size_t id = 0; id < D->ncell; ++id) slot[id] = need[id] ? nslot++ : -1;
+    rec = (slim_rec *)malloc((size_t)(nslot > 0 ? nslot : 1) * sizeof(slim_rec));
+    if (!rec) { free(Qp); free(slot); free(need); return -1; }
 #pragma omp parallel for schedule(dynamic, 64) num_threads(ORC_THREADS(c))
     for (long lin = 0; lin < nrec; ++lin) {
         int i = (int)(lin % nx1) - 1, j = (int)((lin / nx1) % ny1) - 1, k = (int)(lin / ((long)nx1 * ny1)) - 1;
         size_t id = cid(D, i, j, k);
-        if (need[id]) reconstruct_cell(c, G, Qp, i, j, k, &rec[id]);
+        if (need[id]) {
+            cell_rec full;
+            reconstruct_cell(c, G, Qp, i, j, k, &full);
+            slim_from(&full, &rec[slot[id]]);
+        }
     }
 
     /* every face once: axis d, index f in [0, n_d] along d, transverse
@@ -1272,7 +1306,7 @@ static int residuals(const orc_cfg *c, const orc_geom *G, const double *q, doubl
         int o3[3] = {(int)(r0 % ext[0]), (int)((r0 / ext[0]) % ext[1]), (int)(r0 / ((long)ext[0] * ext[1]))};
         int l3[3] = {o3[0], o3[1], o3[2]};
         l3[d] -= 1;
-        if (face_flux(c, G, &rec[cid(D, l3[0], l3[1], l3[2])], &rec[cid(D, o3[0], o3[1], o3[2])], d, o3[0], o3[1],
+        if (face_flux(c, G, &rec[slot[cid(D, l3[0], l3[1], l3[2])]], &rec[slot[cid(D, o3[0], o3[1], o3[2])]], d, o3[0], o3[1],
                       o3[2], dt, &FF[fid * 2 * NV], &FF[fid * 2 * NV + NV]))
             err = 1;
         SW[fid] = face_swept_rate(G, d, o3[0], o3[1], o3[2]);
@@ -1306,6 +1340,7 @@ static int residuals(const orc_cfg *c, const orc_geom *G, const double *q, doubl
     free(fneed);
     free(Qp);
     free(rec);
+    free(slot);
     free(need);
     return err ? -1 : 0;
 }
@@ -1326,7 +1361,9 @@ int orc_operator(const orc_cfg *c, const double *q, double t, double dt, long nc
     for (size_t o = 0; o < nout && rc == 0; ++o) {
         long lin = ncells >= 0 ? cells[o] : (long)o;
         int i = (int)(lin % c->n[0]), j = (int)((lin / c->n[0]) % c->n[1]), k = (int)(lin / ((long)c->n[0] * c->n[1]));
-        double vol = G.cg[cid(&G.D, i, j, k)].vol;
+        cell_geom cg;
+        cell_geometry(&G, i, j, k, &cg);
+        double vol = cg.vol;
         for (int v = 0; v < NV; ++v) {
             L[(size_t)v * nout + o] /= vol;
             dL[(size_t)v * nout + o] /= vol;
@@ -1402,10 +1439,12 @@ int orc_eval_reconstruction(const orc_cfg *c, const double *q, double t, long li
     fill_ghosts(c, D, q, Qp);
     int i = (int)(lin % c->n[0]), j = (int)((lin / c->n[0]) % c->n[1]), k = (int)(lin / ((long)c->n[0] * c->n[1]));
     cell_rec r;
+    slim_rec sr;
     reconstruct_cell(c, &G, Qp, i, j, k, &r);
+    slim_from(&r, &sr);
     for (int p = 0; p < np; ++p) {
         double W[NV], dW[NV][3];
-        rec_eval(&r, &x[p * 3], W, dW);
+        rec_eval(&sr, &x[p * 3], W, dW);
         for (int v = 0; v < NV; ++v) {
             out[(p * NV + v) * 4] = W[v];
             for (int e = 0; e < 3; ++e) out[(p * NV + v) * 4 + 1 + e] = dW[v][e];
@@ -1431,7 +1470,9 @@ double orc_cfl_dt(const orc_cfg *c, const double *q, double t, double cfl)
         double rho = W[0];
         double speed = sqrt(W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / rho;
         double snd = sqrt(c->gamma * pressure_of(c, W) / rho);
-        double hloc = G.cg[cid(&G.D, i, j, k)].h;
+        cell_geom cg;
+        cell_geometry(&G, i, j, k, &cg);
+        double hloc = cg.h;
         double v = hloc / (speed + snd);
         if (v < best) best = v;
     }
@@ -1447,7 +1488,11 @@ int orc_volumes(const orc_cfg *c, double t, double *vol)
     for (int k = 0; k < c->n[2]; ++k)
         for (int j = 0; j < c->n[1]; ++j)
             for (int i = 0; i < c->n[0]; ++i)
-                vol[((size_t)k * c->n[1] + j) * c->n[0] + i] = G.cg[cid(&G.D, i, j, k)].vol;
+            {
+                cell_geom cg;
+                cell_geometry(&G, i, j, k, &cg);
+                vol[((size_t)k * c->n[1] + j) * c->n[0] + i] = cg.vol;
+            }
     geom_free(&G);
     return 0;
 }

@@ -1,0 +1,581 @@
+// Device arithmetic of the HGKS hot path for sm_103a: WENO-AO
+// reconstruction on a uniform mesh of cubes (Sec. 2) and the gas-kinetic
+// flux at a Gauss point (Sec. 3).  Everything is templated on the working
+// precision R (double for the FP64 path, float for the mixed path).
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+// host+device inline: the arithmetic below also compiles for the host so
+// that the operation counter (opcount.cu) can instantiate it
+#ifndef HK_HD
+#define HK_HD __host__ __device__ __forceinline__
+#endif
+
+namespace hk {
+
+// ---------------------------------------------------------------------------
+// math overloads
+// ---------------------------------------------------------------------------
+HK_HD double m_exp(double x) { return exp(x); }
+HK_HD float m_exp(float x) { return expf(x); }
+HK_HD double m_expm1(double x) { return expm1(x); }
+HK_HD float m_expm1(float x) { return expm1f(x); }
+HK_HD double m_erfc(double x) { return erfc(x); }
+HK_HD float m_erfc(float x) { return erfcf(x); }
+HK_HD double m_sqrt(double x) { return sqrt(x); }
+HK_HD float m_sqrt(float x) { return sqrtf(x); }
+HK_HD double m_abs(double x) { return fabs(x); }
+HK_HD double m_max(double a, double b) { return fmax(a, b); }
+HK_HD float m_max(float a, float b) { return fmaxf(a, b); }
+HK_HD float m_abs(float x) { return fabsf(x); }
+
+// Scheme constants, passed by value to every kernel.
+struct Scheme {
+    double gamma;      // ratio of specific heats
+    double K;          // internal degrees of freedom (5 - 3 gamma)/(gamma - 1)
+    double mu, Pr;     // viscosity (0: Euler collision time) and Prandtl number
+    double tau_eps, tau_C;
+    double weno_eps;   // epsilon of the nonlinear weights
+    double Gamma_lin;  // linear weight of each sub-stencil
+    int weno_pow;      // exponent on tau/(beta + eps)
+    int limiter;       // positivity fallback on/off
+};
+
+// Mesh: a uniform grid of cubes with GH = 2 ghost layers in the state
+// arrays and one ghost layer in the reconstruction arrays.
+struct Geo {
+    int nx, ny, nz;          // interior cells
+    int px, py, pz;          // padded state extents (n + 4)
+    int cx, cy, cz;          // reconstruction extents (n + 2)
+    long long pstride;       // px*py*pz: variable stride of padded state arrays
+    long long cstride;       // cx*cy*cz: term stride of coefficient arrays
+    long long ncell;         // nx*ny*nz
+    double h, inv_h;         // cell edge and its inverse
+    int bc[6];               // 0 periodic, 1 reflective per face
+};
+
+HK_HD long long pidx(const Geo &g, int i, int j, int k)
+{
+    return ((long long)(k + 2) * g.py + (j + 2)) * g.px + (i + 2);
+}
+HK_HD long long cidx(const Geo &g, int i, int j, int k)
+{
+    return ((long long)(k + 1) * g.cy + (j + 1)) * g.cx + (i + 1);
+}
+
+// Per-handle device control block: time, step and status.
+struct Ctl {
+    double t, dt;
+    unsigned long long minbits;  // CFL reduction accumulator (bits of a positive double)
+    int active;                  // 1 while the current step has dt > 0
+    int status;                  // bit 0: nonphysical state produced
+    int steps_done;
+    int flagged;                 // cells that took the positivity fallback (last stage)
+};
+
+// ---------------------------------------------------------------------------
+// Maxwellian moments (Sec. 3).  For g = rho (lam/pi)^{(K+3)/2}
+// exp(-lam(|u-U|^2 + xi^2)) the normalised moments factorise,
+// <u^a v^b w^c xi^2d> = <u^a><v^b><w^c><xi^2d>, and each 1D moment obeys
+// <u^{n+2}> = U <u^{n+1}> + (n+1)/(2 lam) <u^n>, on the whole line and on
+// either half line (the boundary term vanishes for n >= 1 at u = 0).
+// ---------------------------------------------------------------------------
+template <typename R> struct Mom {
+    R u[7], v[7], w[7];
+    R xi2, xi4;
+};
+
+template <typename R>
+HK_HD void mom_full_1d(R U, R th, R *m)
+{
+    m[0] = R(1);
+    m[1] = U;
+#pragma unroll
+    for (int n = 2; n < 7; ++n) m[n] = U * m[n - 1] + R(n - 1) * th * m[n - 2];
+}
+
+// half line u > 0 (side = +1) or u < 0 (side = -1):
+// <1> = erfc(-side sqrt(lam) U)/2, <u> = U <1> + side exp(-lam U^2)/(2 sqrt(pi lam))
+template <typename R>
+HK_HD void mom_half_1d(R U, R lam, R th, R side, R *m)
+{
+    const R inv_sqrt_pi = R(0.56418958354775628695);
+    R sl = m_sqrt(lam);
+    m[0] = R(0.5) * m_erfc(-side * sl * U);
+    m[1] = U * m[0] + side * R(0.5) * inv_sqrt_pi * m_exp(-lam * U * U) / sl;
+#pragma unroll
+    for (int n = 2; n < 7; ++n) m[n] = U * m[n - 1] + R(n - 1) * th * m[n - 2];
+}
+
+template <int A, int B, int C, typename R> HK_HD R M3(const Mom<R> &m)
+{
+    return m.u[A] * m.v[B] * m.w[C];
+}
+
+// <u^A v^B w^C psi>, psi = (1, u, v, w, (u^2 + v^2 + w^2 + xi^2)/2)
+template <int A, int B, int C, typename R> HK_HD void psi_m(const Mom<R> &m, R o[5])
+{
+    R m0 = M3<A, B, C>(m);
+    o[0] = m0;
+    o[1] = M3<A + 1, B, C>(m);
+    o[2] = M3<A, B + 1, C>(m);
+    o[3] = M3<A, B, C + 1>(m);
+    o[4] = R(0.5) * (M3<A + 2, B, C>(m) + M3<A, B + 2, C>(m) + M3<A, B, C + 2>(m) + m.xi2 * m0);
+}
+
+// <xi^2 u^A v^B w^C psi>
+template <int A, int B, int C, typename R> HK_HD void psi_xi_m(const Mom<R> &m, R o[5])
+{
+    R m0 = M3<A, B, C>(m);
+    o[0] = m.xi2 * m0;
+    o[1] = m.xi2 * M3<A + 1, B, C>(m);
+    o[2] = m.xi2 * M3<A, B + 1, C>(m);
+    o[3] = m.xi2 * M3<A, B, C + 1>(m);
+    o[4] = R(0.5) * (m.xi2 * (M3<A + 2, B, C>(m) + M3<A, B + 2, C>(m) + M3<A, B, C + 2>(m)) + m.xi4 * m0);
+}
+
+// <(s . psi) u^A v^B w^C psi>
+template <int A, int B, int C, typename R>
+HK_HD void apsi_m(const Mom<R> &m, const R s[5], R o[5])
+{
+    R t[5], q[5];
+    psi_m<A, B, C>(m, t);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) o[k] = s[0] * t[k];
+    psi_m<A + 1, B, C>(m, t);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) o[k] += s[1] * t[k];
+    psi_m<A, B + 1, C>(m, t);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) o[k] += s[2] * t[k];
+    psi_m<A, B, C + 1>(m, t);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) o[k] += s[3] * t[k];
+    psi_m<A + 2, B, C>(m, q);
+    psi_m<A, B + 2, C>(m, t);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) q[k] += t[k];
+    psi_m<A, B, C + 2>(m, t);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) q[k] += t[k];
+    psi_xi_m<A, B, C>(m, t);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) o[k] += R(0.5) * s[4] * (q[k] + t[k]);
+}
+
+// Solve <(a . psi) psi> = b (moments per unit density) in closed form for a
+// Maxwellian with velocity (U, V, W) and lam, written in the peculiar
+// velocity: the moment matrix is block-structured there.
+template <typename R>
+HK_HD void micro_slope(R U, R V, R W, R lam, R Kp3, const R b[5], R a[5])
+{
+    R q2 = U * U + V * V + W * W + Kp3 / (R(2) * lam);
+    R r4 = R(2) * b[4] - q2 * b[0];
+    R r1 = b[1] - U * b[0];
+    R r2 = b[2] - V * b[0];
+    R r3 = b[3] - W * b[0];
+    a[4] = R(4) * lam * lam / Kp3 * (r4 - R(2) * (U * r1 + V * r2 + W * r3));
+    a[1] = R(2) * lam * r1 - U * a[4];
+    a[2] = R(2) * lam * r2 - V * a[4];
+    a[3] = R(2) * lam * r3 - W * a[4];
+    a[0] = b[0] - U * a[1] - V * a[2] - W * a[3] - R(0.5) * a[4] * q2;
+}
+
+template <typename R> struct Prim {
+    R rho, U, V, W, lam, p;
+};
+
+template <typename R> HK_HD Prim<R> primitive(const R Wc[5], R gamma, R Kp3)
+{
+    Prim<R> s;
+    s.rho = Wc[0];
+    R ir = R(1) / Wc[0];
+    s.U = Wc[1] * ir;
+    s.V = Wc[2] * ir;
+    s.W = Wc[3] * ir;
+    R eint = Wc[4] - R(0.5) * (Wc[1] * s.U + Wc[2] * s.V + Wc[3] * s.W);
+    s.p = (gamma - R(1)) * eint;
+    // rho E = rho |U|^2/2 + (K+3) rho/(4 lam)
+    s.lam = Kp3 * Wc[0] / (R(4) * eint);
+    return s;
+}
+
+template <typename R> HK_HD void full_moments(const Prim<R> &s, R K, Mom<R> &m)
+{
+    R th = R(0.5) / s.lam;
+    mom_full_1d(s.U, th, m.u);
+    mom_full_1d(s.V, th, m.v);
+    mom_full_1d(s.W, th, m.w);
+    m.xi2 = K * th;
+    m.xi4 = K * (K + R(2)) * th * th;
+}
+
+// ---------------------------------------------------------------------------
+// Gas-kinetic flux at one Gauss point (Sec. 3), local frame (n_x, n_y, n_z),
+// n_x from the left to the right cell.  Reading: g_l carries u > 0 and g_r
+// u < 0 in eq. (flux), as in the half-space split of Q0.  Returns the flux
+// per unit area F^n and its time derivative, found from the time integrals
+// over dt and dt/2 (eq. expansion-1) in closed form.
+// ---------------------------------------------------------------------------
+template <typename R>
+HK_HD void gks_flux(const R Wl[5], const R dWl[3][5], const R Wr[5], const R dWr[3][5],
+                                         const Scheme &S, R dt, R F[5], R dF[5])
+{
+    const R gamma = R(S.gamma), K = R(S.K), Kp3 = R(S.K) + R(3);
+    const bool prfix = (S.mu > 0.0) && (S.Pr != 1.0);
+
+    R W0[5], dW0[3][5], Fa[5], Fb[5], Fc[5], Sa[5], Sb[5], Sc[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        W0[k] = Fa[k] = Fb[k] = Fc[k] = Sb[k] = Sc[k] = R(0);
+        dW0[0][k] = dW0[1][k] = dW0[2][k] = R(0);
+    }
+    R pside[2];
+
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const R *Wc = side ? Wr : Wl;
+        const R(*dW)[5] = side ? dWr : dWl;
+        Prim<R> s = primitive(Wc, gamma, Kp3);
+        pside[side] = s.p;
+        R ir = R(1) / s.rho;
+        // spatial slopes a_i = M^{-1} dW/dn_i
+        R a[3][5];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            R b[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) b[k] = dW[i][k] * ir;
+            micro_slope(s.U, s.V, s.W, s.lam, Kp3, b, a[i]);
+        }
+        // time slope: <a_1 u + a_2 v + a_3 w + A> = 0
+        Mom<R> m;
+        full_moments(s, K, m);
+        R A[5];
+        {
+            R t1[5], t2[5], t3[5], b[5];
+            apsi_m<1, 0, 0>(m, a[0], t1);
+            apsi_m<0, 1, 0>(m, a[1], t2);
+            apsi_m<0, 0, 1>(m, a[2], t3);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) b[k] = -(t1[k] + t2[k] + t3[k]);
+            micro_slope(s.U, s.V, s.W, s.lam, Kp3, b, A);
+        }
+        // switch u to the half line of this side
+        mom_half_1d(s.U, s.lam, R(0.5) / s.lam, side ? R(-1) : R(1), m.u);
+        R t[5];
+        psi_m<0, 0, 0>(m, t);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) W0[k] += s.rho * t[k];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            apsi_m<0, 0, 0>(m, a[i], t);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) dW0[i][k] += s.rho * t[k];
+        }
+        psi_m<1, 0, 0>(m, t);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) Fa[k] += s.rho * t[k];
+        {
+            R t1[5], t2[5], t3[5];
+            apsi_m<2, 0, 0>(m, a[0], t1);
+            apsi_m<1, 1, 0>(m, a[1], t2);
+            apsi_m<1, 0, 1>(m, a[2], t3);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) Fb[k] += s.rho * (t1[k] + t2[k] + t3[k]);
+        }
+        apsi_m<1, 0, 0>(m, A, t);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) Fc[k] += s.rho * t[k];
+        if (prfix) {
+            R t1[5], t2[5], t3[5];
+            apsi_m<1, 0, 0>(m, a[0], t1);
+            apsi_m<0, 1, 0>(m, a[1], t2);
+            apsi_m<0, 0, 1>(m, a[2], t3);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) Sb[k] += s.rho * (t1[k] + t2[k] + t3[k]);
+            apsi_m<0, 0, 0>(m, A, t);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) Sc[k] += s.rho * t[k];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Sa[k] = W0[k];
+
+    // equilibrium state at the interface and its slopes
+    Prim<R> s0 = primitive(W0, gamma, Kp3);
+    R ir0 = R(1) / s0.rho;
+    R abar[3][5], Abar[5];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        R b[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) b[k] = dW0[i][k] * ir0;
+        micro_slope(s0.U, s0.V, s0.W, s0.lam, Kp3, b, abar[i]);
+    }
+    Mom<R> m0;
+    full_moments(s0, K, m0);
+    R S0b[5];
+    {
+        R t1[5], t2[5], t3[5], b[5];
+        apsi_m<1, 0, 0>(m0, abar[0], t1);
+        apsi_m<0, 1, 0>(m0, abar[1], t2);
+        apsi_m<0, 0, 1>(m0, abar[2], t3);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            S0b[k] = t1[k] + t2[k] + t3[k];
+            b[k] = -S0b[k];
+        }
+        micro_slope(s0.U, s0.V, s0.W, s0.lam, Kp3, b, Abar);
+    }
+    R F0a[5], F0b[5], F0c[5];
+    psi_m<1, 0, 0>(m0, F0a);
+    {
+        R t1[5], t2[5], t3[5];
+        apsi_m<2, 0, 0>(m0, abar[0], t1);
+        apsi_m<1, 1, 0>(m0, abar[1], t2);
+        apsi_m<1, 0, 1>(m0, abar[2], t3);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) F0b[k] = t1[k] + t2[k] + t3[k];
+    }
+    apsi_m<1, 0, 0>(m0, Abar, F0c);
+
+    // collision time (Sec. 4)
+    R jump = m_abs((pside[0] - pside[1]) / (pside[0] + pside[1]));
+    R tau;
+    if (S.mu > 0.0)
+        tau = R(S.mu) / s0.p + R(S.tau_C) * jump * dt;
+    else
+        tau = (R(S.tau_eps) + R(S.tau_C) * jump) * dt;
+
+    // F = (4 Fh(dt/2) - Fh(dt))/dt and dF = 4 (Fh(dt) - 2 Fh(dt/2))/dt^2 for
+    // Fh(delta) = sum_j q_j(delta) M_j, with q_j the time integrals of the
+    // factors of eq. (flux); the combinations c_j, d_j below are those
+    // integrals worked out with e2 = exp(-dt/(2 tau)), e1 = e2^2.
+    R x = dt / (R(2) * tau);
+    R om = -m_expm1(-x);  // 1 - e2
+    R e2 = R(1) - om;
+    R e1 = e2 * e2;
+    R r = tau / dt;
+    R E3 = om * (R(3) - e2);
+    R Dq = om * om;
+    R c3 = r * E3, c0 = R(1) - c3, c2 = -tau * c0, c5 = -tau * c3;
+    R c1 = tau * (e1 - R(2) * e2 - R(1)) + R(2) * tau * r * E3;
+    R c4 = -tau - c1;
+    R d0 = R(4) * r * Dq / dt, d3 = -d0, d2 = R(1) - tau * d0, d5 = tau * d0;
+    R d1 = R(4) * r * (e2 - e1) - R(8) * r * r * Dq, d4 = -d1;
+
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        F[k] = s0.rho * (c0 * F0a[k] + c1 * F0b[k] + c2 * F0c[k]) + c3 * Fa[k] + c4 * Fb[k] + c5 * Fc[k];
+        dF[k] = s0.rho * (d0 * F0a[k] + d1 * F0b[k] + d2 * F0c[k]) + d3 * Fa[k] + d4 * Fb[k] + d5 * Fc[k];
+    }
+    if (prfix) {
+        // heat flux about U0 of the time-integrated distribution:
+        // q = F_E - U0.F_m + |U0|^2/2 F_rho - U0_x (S_E - U0.S_m + |U0|^2/2 S_rho),
+        // S the psi-moments of the same terms (S of the g0 A-term is -S0b).
+        R uu = R(0.5) * (s0.U * s0.U + s0.V * s0.V + s0.W * s0.W);
+        R Sx[5], Sd[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            R s0b = s0.rho * S0b[k];
+            Sx[k] = c0 * Sa[k] + (c1 - c2) * s0b + c3 * Sa[k] + c4 * Sb[k] + c5 * Sc[k];
+            Sd[k] = d0 * Sa[k] + (d1 - d2) * s0b + d3 * Sa[k] + d4 * Sb[k] + d5 * Sc[k];
+        }
+        // the g0 and initial terms both carry W0-like psi moments: the g0
+        // term's zeroth piece is W0 itself and the half-space pieces sum to W0
+        R qf = F[4] - (s0.U * F[1] + s0.V * F[2] + s0.W * F[3]) + uu * F[0]
+               - s0.U * (Sx[4] - (s0.U * Sx[1] + s0.V * Sx[2] + s0.W * Sx[3]) + uu * Sx[0]);
+        R qd = dF[4] - (s0.U * dF[1] + s0.V * dF[2] + s0.W * dF[3]) + uu * dF[0]
+               - s0.U * (Sd[4] - (s0.U * Sd[1] + s0.V * Sd[2] + s0.W * Sd[3]) + uu * Sd[0]);
+        R fac = R(1) / R(S.Pr) - R(1);
+        F[4] += fac * qf;
+        dF[4] += fac * qd;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// WENO-AO reconstruction on a uniform mesh of cubes (Sec. 2).
+//
+// In scaled coordinates X = (x - x_c)/h the row of the big-stencil least
+// squares for neighbour offset (i, j, k) is [i, j, k, i^2, j^2, k^2, ij, ik,
+// jk]; over the 18 cells of S the normal matrix is diag(10 I_3,
+// 6 I_3 + 4 11^T, 4 I_3), so P0 has the closed form
+//   a_d  = (1/10) sum o_d dQ,   a_de = (1/4) sum o_d o_e dQ,
+//   a_dd = (1/6)(s_dd - (2/9)(s_xx + s_yy + s_zz)),  s_dd = sum o_d^2 dQ.
+// A sub-stencil {c, s_a e_a, s_b e_b, s_a e_a + s_b e_b, s_c e_c} gives
+//   b_a = s_a (2 dQ_a - dQ_b + dQ_ab)/3, b_b = s_b (2 dQ_b - dQ_a + dQ_ab)/3,
+//   b_c = s_c dQ_c.
+// Smoothness indicators (eq. indicator, each multi-index once):
+//   beta_m = |b|^2,
+//   beta_0 = sum_d [a_d^2 + (4 a_dd^2 + sum_{e != d} a_de^2)/12]
+//            + 4 sum_d a_dd^2 + sum_{d<e} a_de^2.
+// ---------------------------------------------------------------------------
+template <typename R> struct Stencil {
+    // dQ of the 18 neighbours: face neighbours f[d][0/1] (-/+), edge
+    // neighbours e[plane][sa][sb] for planes (x,y), (y,z), (z,x)
+    R f[3][2];
+    R e[3][2][2];
+};
+
+template <typename R> HK_HD void big_stencil_P0(const Stencil<R> &st, R a[9])
+{
+    // linear: sum over offsets of o_d dQ; face cells and the 8 edge cells with o_d != 0
+    R sd[3], sdd[3], sde[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        // edges in plane (d, d+1) and plane (d-1, d) (= plane index (d+2)%3 with d second)
+        int p1 = d, p2 = (d + 2) % 3;
+        R lin = st.f[d][1] - st.f[d][0];
+        R quad = st.f[d][1] + st.f[d][0];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            // plane p1: d is the first axis
+            lin += st.e[p1][1][s] - st.e[p1][0][s];
+            quad += st.e[p1][1][s] + st.e[p1][0][s];
+            // plane p2: d is the second axis
+            lin += st.e[p2][s][1] - st.e[p2][s][0];
+            quad += st.e[p2][s][1] + st.e[p2][s][0];
+        }
+        sd[d] = lin;
+        sdd[d] = quad;
+        // cross moment sum o_a o_b dQ over the plane (a, b) = (d, d+1)
+        sde[d] = st.e[d][1][1] + st.e[d][0][0] - st.e[d][1][0] - st.e[d][0][1];
+    }
+    const R tr = sdd[0] + sdd[1] + sdd[2];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        a[d] = R(0.1) * sd[d];
+        a[3 + d] = (sdd[d] - R(2.0 / 9.0) * tr) * R(1.0 / 6.0);
+    }
+    // xy = plane 0, xz = plane 2 (z,x) -> same product, yz = plane 1
+    a[6] = R(0.25) * sde[0];
+    a[7] = R(0.25) * sde[2];
+    a[8] = R(0.25) * sde[1];
+}
+
+template <typename R> HK_HD R beta_quadratic(const R a[9])
+{
+    const R ax = a[0], ay = a[1], az = a[2], axx = a[3], ayy = a[4], azz = a[5], axy = a[6], axz = a[7], ayz = a[8];
+    const R d2 = R(4) * (axx * axx + ayy * ayy + azz * azz);
+    const R m2 = axy * axy + axz * axz + ayz * ayz;
+    return ax * ax + ay * ay + az * az + (d2 + R(2) * m2) * R(1.0 / 12.0) + d2 + m2;
+}
+
+// sub-stencil m = 8 p + s: plane (a, b) = (p, p+1), out-of-plane c = p+2,
+// signs in the order (+++), (-++), (+-+), (--+), (++-), (-+-), (+--), (---)
+template <typename R>
+HK_HD void sub_stencil(const Stencil<R> &st, int p, int s, R b[3])
+{
+    const int sa = (s & 1) ? 0 : 1, sb = (s & 2) ? 0 : 1, sc = (s & 4) ? 0 : 1;
+    const int a = p, bb = (p + 1) % 3, c = (p + 2) % 3;
+    const R qa = st.f[a][sa], qb = st.f[bb][sb], qab = st.e[p][sa][sb], qc = st.f[c][sc];
+    const R ba = (R(2) * qa - qb + qab) * R(1.0 / 3.0);
+    const R bbv = (R(2) * qb - qa + qab) * R(1.0 / 3.0);
+    b[a] = sa ? ba : -ba;
+    b[bb] = sb ? bbv : -bbv;
+    b[c] = sc ? qc : -qc;
+}
+
+// rigorous bound of |P(X) - Q_c| over the cell (|X_d| <= 1/2)
+template <typename R> HK_HD R bound_linear(const R b[3])
+{
+    return R(0.5) * (m_abs(b[0]) + m_abs(b[1]) + m_abs(b[2]));
+}
+template <typename R> HK_HD R bound_quadratic(const R a[9])
+{
+    return R(0.5) * (m_abs(a[0]) + m_abs(a[1]) + m_abs(a[2]))
+           + R(1.0 / 6.0) * (m_abs(a[3]) + m_abs(a[4]) + m_abs(a[5]))
+           + R(0.25) * (m_abs(a[6]) + m_abs(a[7]) + m_abs(a[8]));
+}
+
+// value of Q_c + sum c_n p_n at scaled X (p = X, Y, Z, X^2-1/12, ..., XY, XZ, YZ)
+template <typename R> HK_HD R poly9(const R c[9], const R X[3])
+{
+    const R tw = R(1.0 / 12.0);
+    return c[0] * X[0] + c[1] * X[1] + c[2] * X[2] + c[3] * (X[0] * X[0] - tw) + c[4] * (X[1] * X[1] - tw)
+           + c[5] * (X[2] * X[2] - tw) + c[6] * X[0] * X[1] + c[7] * X[0] * X[2] + c[8] * X[1] * X[2];
+}
+
+
+// P~ - Q_c and its physical gradient at scaled X (ih = 1/h)
+template <typename R> HK_HD void poly_value_grad(const R c[9], const R X[3], R ih, R &s, R grad[3])
+{
+    s = poly9(c, X);
+    grad[0] = (c[0] + R(2) * c[3] * X[0] + c[6] * X[1] + c[7] * X[2]) * ih;
+    grad[1] = (c[1] + R(2) * c[4] * X[1] + c[6] * X[0] + c[8] * X[2]) * ih;
+    grad[2] = (c[2] + R(2) * c[5] * X[2] + c[7] * X[0] + c[8] * X[1]) * ih;
+}
+
+// WENO-AO combination for one conserved variable (Sec. 2): P0, the 24
+// linear P_m, their indicators, tau of eq. (para), the nonlinear weights of
+// eq. (nonlinear) and P~ = (w0/g0) P0 + sum (w_m - w0 g_m/g0) P_m, returned
+// as the 9 coefficients of one quadratic; rad receives a rigorous bound of
+// |P_m(X) - Q_c| over the cell for all 25 polynomials.
+template <typename R>
+HK_HD void weno_ao(const Stencil<R> &st, const Scheme &S, R out[9], R &rad)
+{
+    const R g0 = R(1.0 - 24.0 * S.Gamma_lin), gm = R(S.Gamma_lin), eps = R(S.weno_eps);
+    const R ig0 = R(1) / g0;
+    R a[9];
+    big_stencil_P0(st, a);
+    const R beta0 = beta_quadratic(a);
+    R r = bound_quadratic(a);
+    // pass 1: indicators of the 24 linear polynomials and tau
+    R tau = R(0);
+#pragma unroll 4
+    for (int m = 0; m < 24; ++m) {
+        R b[3];
+        sub_stencil(st, m >> 3, m & 7, b);
+        const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+        tau += m_abs(beta0 - bm);
+        r = m_max(r, bound_linear(b));
+    }
+    tau *= R(1.0 / 24.0);
+    rad = r;
+    // pass 2: weights and the combination, normalised at the end
+    const R x0 = tau / (beta0 + eps);
+    const R w0 = g0 * (R(1) + (S.weno_pow == 2 ? x0 * x0 : x0));
+    R wsum = w0;
+    R lin[3] = {R(0), R(0), R(0)};
+#pragma unroll 4
+    for (int m = 0; m < 24; ++m) {
+        R b[3];
+        sub_stencil(st, m >> 3, m & 7, b);
+        const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+        const R xm = tau / (bm + eps);
+        const R wm = gm * (R(1) + (S.weno_pow == 2 ? xm * xm : xm));
+        wsum += wm;
+        const R cm = wm - w0 * gm * ig0;
+        lin[0] += cm * b[0];
+        lin[1] += cm * b[1];
+        lin[2] += cm * b[2];
+    }
+    const R iw = R(1) / wsum;
+    const R f0 = w0 * ig0;
+#pragma unroll
+    for (int n = 0; n < 9; ++n) out[n] = iw * (f0 * a[n] + (n < 3 ? lin[n] : R(0)));
+}
+
+// Sufficient test that no P_m gives negative density or pressure anywhere in
+// the cell, from the cell averages and the bounds rad[v]; when it fails the
+// literal check of the fallback (Sec. 4) decides.
+template <typename R> HK_HD bool positivity_certain(const R qc[5], const R rad[5], R gamma)
+{
+    const R rho_min = qc[0] - rad[0];
+    if (!(rho_min > R(0))) return false;
+    R m2 = R(0);
+#pragma unroll
+    for (int d = 1; d <= 3; ++d) {
+        const R mm = m_abs(qc[d]) + rad[d];
+        m2 += mm * mm;
+    }
+    const R e_min = qc[4] - rad[4];
+    const R p_low = (gamma - R(1)) * (e_min - R(0.5) * m2 / rho_min);
+    const R margin = R(sizeof(R) == 8 ? 1e-10 : 1e-4) * (m_abs(qc[4]) + rad[4] + R(0.5) * m2 / rho_min);
+    return p_low > margin;
+}
+
+}  // namespace hk

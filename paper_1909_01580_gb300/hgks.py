@@ -1,0 +1,276 @@
+"""Thin ctypes binding of libhgks.so (include/hgks.h), same names as the C ABI.
+
+Argument marshalling only: every step of the scheme runs in the CUDA
+kernels of the library.  Host buffers are NumPy arrays; device buffers are
+CUDA torch tensors (passed as raw pointers).  There is no CPU fallback: if
+the library is missing or no GPU is usable, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+HGKS_FP64 = 0
+HGKS_MIXED = 1
+HGKS_BC_PERIODIC = 0
+HGKS_BC_REFLECTIVE = 1
+HGKS_OK = 0
+HGKS_E_INVALID = -1
+HGKS_E_NOMEM = -2
+HGKS_E_CUDA = -3
+HGKS_E_NONPHYSICAL = -4
+HGKS_E_TIMEOUT = -5
+HGKS_E_STATE = -6
+
+# every symbol include/hgks.h declares
+EXPORTS = ("hgks_create", "hgks_set_option", "hgks_set_state", "hgks_get_state", "hgks_step", "hgks_flux",
+           "hgks_reconstruct", "hgks_point_flux", "hgks_set_timing", "hgks_get_timing", "hgks_launch_count", "hgks_device_bytes", "hgks_last_error",
+           "hgks_destroy")
+
+
+class HgksError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"hgks error {code}: {msg}")
+        self.code = code
+
+
+class hgks_grid_t(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int * 3),
+        ("lo", ctypes.c_double * 3),
+        ("hi", ctypes.c_double * 3),
+        ("mesh", ctypes.c_int),
+        ("mesh_amp", ctypes.c_double),
+        ("mesh_omega", ctypes.c_double),
+        ("precision", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libhgks.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise HgksError(HGKS_E_CUDA, f"CUDA library not built: {path}")
+    L = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    dp = P(ctypes.c_double)
+    vp = ctypes.c_void_p
+    L.hgks_create.argtypes = [P(hgks_grid_t), ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                              P(ctypes.c_int), vp, P(vp)]
+    L.hgks_set_option.argtypes = [vp, ctypes.c_char_p, ctypes.c_double]
+    L.hgks_set_state.argtypes = [vp, vp, ctypes.c_int, ctypes.c_double]
+    L.hgks_get_state.argtypes = [vp, vp, ctypes.c_int, dp]
+    L.hgks_step.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp,
+                            P(ctypes.c_int)]
+    L.hgks_flux.argtypes = [vp, ctypes.c_double, vp, vp, ctypes.c_int]
+    L.hgks_reconstruct.argtypes = [vp, vp, vp]
+    L.hgks_point_flux.argtypes = [ctypes.c_int, vp, vp, ctypes.c_double, dp, ctypes.c_int, vp, vp]
+    L.hgks_set_timing.argtypes = [vp, ctypes.c_int]
+    L.hgks_set_timing.restype = ctypes.c_int
+    L.hgks_get_timing.argtypes = [vp, dp, P(ctypes.c_ulonglong)]
+    L.hgks_get_timing.restype = ctypes.c_int
+    L.hgks_launch_count.argtypes = [vp]
+    L.hgks_launch_count.restype = ctypes.c_ulonglong
+    L.hgks_device_bytes.argtypes = [vp]
+    L.hgks_device_bytes.restype = ctypes.c_ulonglong
+    L.hgks_last_error.argtypes = [vp]
+    L.hgks_last_error.restype = ctypes.c_char_p
+    L.hgks_destroy.argtypes = [vp]
+    L.hgks_destroy.restype = None
+    for name in ("hgks_create", "hgks_set_option", "hgks_set_state", "hgks_get_state", "hgks_step", "hgks_flux",
+                 "hgks_reconstruct", "hgks_point_flux"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc, handle=None):
+    if rc != HGKS_OK:
+        msg = load().hgks_last_error(handle)
+        raise HgksError(rc, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """(pointer, on_device) of a NumPy array or a CUDA torch tensor (FP64, contiguous)."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host buffers must be C-contiguous float64")
+        return a.ctypes.data, 0
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise ValueError("device buffers must be contiguous float64")
+        return a.data_ptr(), int(a.is_cuda)
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+# ---- functions with the C names -------------------------------------------------------------
+
+def hgks_create(n, lo, hi, gamma=1.4, mu=0.0, Pr=1.0, bc=(0, 0, 0, 0, 0, 0), precision=HGKS_FP64, stream=None):
+    g = hgks_grid_t()
+    for d in range(3):
+        g.n[d], g.lo[d], g.hi[d] = int(n[d]), float(lo[d]), float(hi[d])
+    g.mesh, g.mesh_amp, g.mesh_omega, g.precision = 0, 0.0, 0.0, int(precision)
+    bcs = (ctypes.c_int * 6)(*[int(b) for b in bc])
+    out = ctypes.c_void_p()
+    st = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(load().hgks_create(ctypes.byref(g), float(gamma), float(mu), float(Pr), bcs, st, ctypes.byref(out)))
+    return out.value
+
+
+def hgks_set_option(h, key, value):
+    _check(load().hgks_set_option(h, key.encode(), float(value)), h)
+
+
+def hgks_set_state(h, q, t=0.0):
+    p, dev = _ptr(q)
+    _check(load().hgks_set_state(h, p, dev, float(t)), h)
+
+
+def hgks_get_state(h, q):
+    p, dev = _ptr(q)
+    t = ctypes.c_double()
+    _check(load().hgks_get_state(h, p, dev, ctypes.byref(t)), h)
+    return t.value
+
+
+def hgks_step(h, nsteps, cfl=0.35, dt_fixed=0.0, t_end=float("inf"), sync=True):
+    t = ctypes.c_double()
+    done = ctypes.c_int()
+    if sync:
+        _check(load().hgks_step(h, int(nsteps), float(cfl), float(dt_fixed), float(t_end), ctypes.byref(t),
+                                ctypes.byref(done)), h)
+        return t.value, done.value
+    _check(load().hgks_step(h, int(nsteps), float(cfl), float(dt_fixed), float(t_end), None, None), h)
+    return None
+
+
+def hgks_flux(h, dt, L, dL):
+    pl, dev = _ptr(L)
+    pd, dev2 = _ptr(dL)
+    if dev != dev2:
+        raise ValueError("L and dL must both be host or both be device buffers")
+    _check(load().hgks_flux(h, float(dt), pl, pd, dev), h)
+
+
+def hgks_reconstruct(h, ncell):
+    coef = np.zeros((ncell, 5, 9))
+    flag = np.zeros(ncell, dtype=np.int32)
+    _check(load().hgks_reconstruct(h, coef.ctypes.data, flag.ctypes.data), h)
+    return coef, flag
+
+
+def hgks_point_flux(inp, dt, params, precision=HGKS_FP64, ug=None):
+    inp = np.ascontiguousarray(inp, dtype=np.float64).reshape(-1, 40)
+    n = inp.shape[0]
+    F = np.zeros((n, 5))
+    dF = np.zeros((n, 5))
+    ugp = None
+    if ug is not None:
+        ug = np.ascontiguousarray(np.broadcast_to(ug, (n, 3)), dtype=np.float64)
+        ugp = ug.ctypes.data
+    par = (ctypes.c_double * 5)(*[float(x) for x in params])
+    _check(load().hgks_point_flux(n, inp.ctypes.data, ugp, float(dt), par, int(precision), F.ctypes.data,
+                                  dF.ctypes.data))
+    return F, dF
+
+
+PHASES = ("halo", "recon", "flux", "update", "cfl")
+
+
+def hgks_set_timing(h, enable):
+    _check(load().hgks_set_timing(h, int(bool(enable))), h)
+
+
+def hgks_get_timing(h):
+    """{phase: (ms, launches)} accumulated since hgks_set_timing."""
+    ms = (ctypes.c_double * 5)()
+    nl = (ctypes.c_ulonglong * 5)()
+    _check(load().hgks_get_timing(h, ms, nl), h)
+    return {name: (ms[i], int(nl[i])) for i, name in enumerate(PHASES)}
+
+
+def hgks_launch_count(h) -> int:
+    return int(load().hgks_launch_count(h))
+
+
+def hgks_device_bytes(h) -> int:
+    return int(load().hgks_device_bytes(h))
+
+
+def hgks_last_error(h=None) -> str:
+    m = load().hgks_last_error(h)
+    return m.decode() if m else ""
+
+
+def hgks_destroy(h):
+    if h:
+        load().hgks_destroy(h)
+
+
+class Solver:
+    """Convenience owner of one handle (still only marshalling)."""
+
+    def __init__(self, n, lo, hi, gamma=1.4, mu=0.0, Pr=1.0, bc=(0,) * 6, precision=HGKS_FP64, stream=None,
+                 **options):
+        self.n = tuple(int(x) for x in n)
+        self.h = hgks_create(self.n, lo, hi, gamma, mu, Pr, bc, precision, stream)
+        for k, v in options.items():
+            hgks_set_option(self.h, k, v)
+
+    @property
+    def ncell(self):
+        return self.n[0] * self.n[1] * self.n[2]
+
+    def set_state(self, q, t=0.0):
+        if isinstance(q, np.ndarray):
+            q = np.ascontiguousarray(q, dtype=np.float64)
+        hgks_set_state(self.h, q, t)
+
+    def get_state(self):
+        q = np.zeros((5, self.n[2], self.n[1], self.n[0]))
+        t = hgks_get_state(self.h, q)
+        return q, t
+
+    def step(self, nsteps, cfl=0.35, dt_fixed=0.0, t_end=float("inf"), sync=True):
+        return hgks_step(self.h, nsteps, cfl, dt_fixed, t_end, sync)
+
+    def flux(self, dt):
+        L = np.zeros((5, self.n[2], self.n[1], self.n[0]))
+        dL = np.zeros_like(L)
+        hgks_flux(self.h, dt, L, dL)
+        return L, dL
+
+    def reconstruct(self):
+        return hgks_reconstruct(self.h, self.ncell)
+
+    @property
+    def launches(self):
+        return hgks_launch_count(self.h)
+
+    def close(self):
+        if self.h:
+            hgks_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,363 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, on the
+same seeded inputs: point flux, reconstruction, the operator L and dL/dt,
+10-step runs, full-size sampled cells, and the invariants that hold at any
+size.  Tolerances: FP64 path max relative difference (per variable, max
+|diff| / max |oracle|) <= 1e-11; dL/dt <= 1e-10 because the oracle forms it
+from a 2x2 solve of time integrals that cancels about log10(F/(dt dF))
+digits; mixed path against the FP32 unit round-off."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_01580_gb300 import hgks
+from paper_1909_01580_gb300 import workloads as W
+from tests._cases import max_rel, random_point_inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-11
+TOL_DT = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    hgks.load()
+
+
+def _solver(n, lo, hi, **kw):
+    return hgks.Solver(n, lo, hi, **kw)
+
+
+def _box_for(n, h):
+    return (0.0, 0.0, 0.0), tuple(n[d] * h for d in range(3))
+
+
+# ---------------------------------------------------------------- point flux
+
+@pytest.mark.parametrize("mu,Pr", [(0.0, 1.0), (0.02, 1.0), (0.02, 0.72)])
+def test_point_flux_fp64(mu, Pr):
+    rng = np.random.default_rng(11)
+    inp = random_point_inputs(rng, 48)
+    dt = 0.05
+    cfg = oracle.make_cfg((4, 4, 4), mu=mu, Pr=Pr)
+    Fo, dFo = oracle.point_flux(cfg, inp, dt)
+    F, dF = hgks.hgks_point_flux(inp, dt, (1.4, mu, Pr, 0.01, 1.0), hgks.HGKS_FP64)
+    assert max_rel(F, Fo, axis_vars=1) <= 1e-12
+    assert max_rel(dF, dFo, axis_vars=1) <= TOL_DT
+
+
+def test_point_flux_moving_grid_fp64():
+    rng = np.random.default_rng(12)
+    inp = random_point_inputs(rng, 32)
+    ug = rng.uniform(-0.3, 0.3, (32, 3))
+    cfg = oracle.make_cfg((4, 4, 4), mu=0.01, Pr=0.72)
+    Fo, dFo = oracle.point_flux(cfg, inp, 0.02, ug=ug)
+    F, dF = hgks.hgks_point_flux(inp, 0.02, (1.4, 0.01, 0.72, 0.01, 1.0), hgks.HGKS_FP64, ug=ug)
+    assert max_rel(F, Fo, axis_vars=1) <= 1e-12
+    assert max_rel(dF, dFo, axis_vars=1) <= TOL_DT
+
+
+def test_point_flux_mixed_fp32():
+    rng = np.random.default_rng(13)
+    inp = random_point_inputs(rng, 48)
+    cfg = oracle.make_cfg((4, 4, 4))
+    Fo, dFo = oracle.point_flux(cfg, inp, 0.05)
+    F, dF = hgks.hgks_point_flux(inp, 0.05, (1.4, 0.0, 1.0, 0.01, 1.0), hgks.HGKS_MIXED)
+    assert max_rel(F, Fo, axis_vars=1) <= 2e-5
+    assert max_rel(dF, dFo, axis_vars=1) <= 1e-3
+
+
+# ---------------------------------------------------------------- reconstruction
+
+def _recon_case(name):
+    if name == "smooth_ragged":
+        n = (13, 11, 9)
+        lo, hi = _box_for(n, 1.0 / 13)
+        q = W.smooth_random(n, seed=21, lo=lo, hi=hi, amp=0.2)
+        return n, lo, hi, q, dict()
+    if name == "octant_reflective":
+        n = (10, 10, 10)
+        q = W.octant_riemann(n, seed=3)
+        return n, (0, 0, 0), (1, 1, 1), q, dict(bc=(1,) * 6)
+    if name == "tgv":
+        n = (12, 12, 12)
+        q, lo, hi = W.taylor_green(n)
+        return n, lo, hi, q, dict()
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("case", ["smooth_ragged", "octant_reflective", "tgv"])
+def test_reconstruction_parity(case):
+    n, lo, hi, q, kw = _recon_case(case)
+    cfg = oracle.make_cfg(n, lo, hi, **kw)
+    coef_o, flag_o, _ = oracle.reconstruct(cfg, q)
+    s = _solver(n, lo, hi, **kw)
+    s.set_state(q)
+    coef, flag = s.reconstruct()
+    s.close()
+    assert (flag == flag_o).all()
+    for v in range(5):
+        ref = coef_o[:, v, 1:]
+        scale = max(np.abs(ref).max(), 1e-300)
+        assert np.abs(coef[:, v, :] - ref).max() <= 1e-12 * scale, (case, v)
+
+
+def test_positivity_fallback_fires_and_matches():
+    """A near-vacuum pocket makes the linear polynomials negative: the
+    fallback fires on the same cells as in the oracle."""
+    n = (8, 8, 8)
+    q = W.octant_riemann(n, seed=5)
+    q[:, 3:5, 3:5, 3:5] *= 1e-3  # tiny density and energy in a block
+    q[4, 3:5, 3:5, 3:5] *= 1e-3
+    cfg = oracle.make_cfg(n, (0, 0, 0), (1, 1, 1), bc=(1,) * 6)
+    coef_o, flag_o, _ = oracle.reconstruct(cfg, q)
+    assert flag_o.sum() > 0
+    s = _solver(n, (0, 0, 0), (1, 1, 1), bc=(1,) * 6)
+    s.set_state(q)
+    coef, flag = s.reconstruct()
+    s.close()
+    assert (flag == flag_o).all()
+    assert np.abs(coef[flag == 1]).max() == 0.0
+
+
+# ---------------------------------------------------------------- operator L, dL/dt
+
+@pytest.mark.parametrize("case,mu,Pr", [("smooth_ragged", 1e-3, 0.72), ("octant_reflective", 0.0, 1.0),
+                                        ("tgv", 1.0 / 1600, 0.72)])
+def test_operator_parity(case, mu, Pr):
+    n, lo, hi, q, kw = _recon_case(case)
+    cfg = oracle.make_cfg(n, lo, hi, mu=mu, Pr=Pr, **kw)
+    dt = oracle.cfl_dt(cfg, q, 0.35)
+    Lo, dLo = oracle.operator(cfg, q, dt)
+    s = _solver(n, lo, hi, mu=mu, Pr=Pr, **kw)
+    s.set_state(q)
+    L, dL = s.flux(dt)
+    s.close()
+    assert max_rel(L, Lo) <= TOL, max_rel(L, Lo)
+    assert max_rel(dL, dLo) <= TOL_DT, max_rel(dL, dLo)
+
+
+# ---------------------------------------------------------------- 10-step runs
+
+def test_ten_steps_density_advection_16():
+    """Density advection on 16^3 at CFL 0.5 to t = 0.2: 10 steps, the CFL
+    step reduced on the device; parity with the oracle run."""
+    n = (16, 16, 16)
+    q0 = W.density_advection(n)
+    cfg = oracle.make_cfg(n)
+    qo, to, done_o, _ = oracle.step(cfg, q0, 0.0, 100, cfl=0.5, t_end=0.2)
+    s = _solver(n, (0, 0, 0), (2, 2, 2))
+    s.set_state(q0)
+    t, done = s.step(100, cfl=0.5, t_end=0.2)
+    q, t2 = s.get_state()
+    s.close()
+    assert done_o == 10 and done == 10
+    assert abs(t - 0.2) < 1e-14 and abs(t2 - 0.2) < 1e-14
+    assert max_rel(q, qo) <= TOL, max_rel(q, qo)
+    exact = W.density_advection(n, t=0.2)
+    l1 = float(np.abs(q[0] - exact[0]).sum() * (2.0 / 16) ** 3)
+    assert l1 < 5e-3
+
+
+@pytest.mark.parametrize("case,nsteps", [("tgv16", 10), ("octant16", 6), ("smooth_ragged", 10)])
+def test_multi_step_parity_fixed_dt(case, nsteps):
+    if case == "tgv16":
+        n = (16, 16, 16)
+        q0, lo, hi = W.taylor_green(n)
+        kw = dict(mu=1.0 / 1600, Pr=0.72)
+    elif case == "octant16":
+        n = (16, 16, 16)
+        q0 = W.octant_riemann(n, seed=0)
+        lo, hi = (0, 0, 0), (1, 1, 1)
+        kw = dict(bc=(1,) * 6)
+    else:
+        n, lo, hi, q0, kw = _recon_case("smooth_ragged")
+        kw = dict(mu=1e-3, Pr=0.72)
+    cfg = oracle.make_cfg(n, lo, hi, **kw)
+    dt = oracle.cfl_dt(cfg, q0, 0.35)
+    qo, _, _, _ = oracle.step(cfg, q0, 0.0, nsteps, dt_fixed=dt)
+    s = _solver(n, lo, hi, **kw)
+    s.set_state(q0)
+    t, done = s.step(nsteps, dt_fixed=dt)
+    q, _ = s.get_state()
+    s.close()
+    assert done == nsteps and abs(t - nsteps * dt) < 1e-12
+    assert max_rel(q, qo) <= TOL, (case, max_rel(q, qo))
+
+
+# ---------------------------------------------------------------- full size
+
+def test_full_size_sampled_tgv128():
+    """TGV 128^3 (the benchmark workload): L and dL/dt at sampled cells
+    against the oracle, which evaluates only those cells."""
+    n = (128, 128, 128)
+    q, lo, hi = W.taylor_green(n)
+    mu, Pr = 1.0 / 1600, 0.72
+    cfg = oracle.make_cfg(n, lo, hi, mu=mu, Pr=Pr)
+    dt = 1.5e-3
+    rng = np.random.default_rng(0)
+    cells = np.concatenate([rng.choice(n[0] ** 3, 120, replace=False),
+                            [0, 127, 128 * 127, n[0] ** 3 - 1]])  # corners: periodic wrap
+    Lo, dLo = oracle.operator(cfg, q, dt, cells=cells)
+    s = _solver(n, lo, hi, mu=mu, Pr=Pr)
+    s.set_state(q)
+    L, dL = s.flux(dt)
+    s.close()
+    Ls = L.reshape(5, -1)[:, cells]
+    dLs = dL.reshape(5, -1)[:, cells]
+    assert max_rel(Ls, Lo) <= TOL, max_rel(Ls, Lo)
+    assert max_rel(dLs, dLo) <= TOL_DT, max_rel(dLs, dLo)
+
+
+def test_full_size_sampled_octant128_reflective():
+    n = (128, 128, 128)
+    q = W.octant_riemann(n, seed=1)
+    cfg = oracle.make_cfg(n, (0, 0, 0), (1, 1, 1), bc=(1,) * 6)
+    dt = 1e-3
+    cells = []
+    for (i, j, k) in [(63, 63, 63), (64, 64, 64), (0, 0, 0), (127, 127, 127), (63, 10, 100), (0, 64, 127),
+                      (64, 63, 0), (5, 5, 64)]:
+        cells.append(i + 128 * (j + 128 * k))
+    Lo, dLo = oracle.operator(cfg, q, dt, cells=cells)
+    s = _solver(n, (0, 0, 0), (1, 1, 1), bc=(1,) * 6)
+    s.set_state(q)
+    L, dL = s.flux(dt)
+    s.close()
+    Ls = L.reshape(5, -1)[:, cells]
+    dLs = dL.reshape(5, -1)[:, cells]
+    assert max_rel(Ls, Lo) <= TOL, max_rel(Ls, Lo)
+    assert max_rel(dLs, dLo) <= TOL_DT, max_rel(dLs, dLo)
+
+
+def test_conservation_tgv128_three_steps():
+    n = (128, 128, 128)
+    q0, lo, hi = W.taylor_green(n)
+    s = _solver(n, lo, hi, mu=1.0 / 1600, Pr=0.72)
+    s.set_state(q0)
+    t, done = s.step(3, cfl=0.35)
+    q, _ = s.get_state()
+    s.close()
+    assert done == 3
+    tot0 = q0.reshape(5, -1).sum(axis=1)
+    tot1 = q.reshape(5, -1).sum(axis=1)
+    scale = np.abs(q0).reshape(5, -1).sum(axis=1)
+    assert (np.abs(tot1 - tot0) <= 1e-13 * scale).all(), (tot1 - tot0) / scale
+
+
+def test_free_stream_gpu():
+    n = (24, 20, 16)
+    lo, hi = _box_for(n, 0.05)
+    q0 = W.uniform_flow(n, rho=1.2, u=(0.3, -0.5, 0.2), p=0.8)
+    for prec in (hgks.HGKS_FP64, hgks.HGKS_MIXED):
+        s = _solver(n, lo, hi, precision=prec)
+        s.set_state(q0)
+        s.step(3, cfl=0.35)
+        q, _ = s.get_state()
+        s.close()
+        assert np.abs(q - q0).max() <= (2e-14 if prec == hgks.HGKS_FP64 else 2e-6)
+
+
+# ---------------------------------------------------------------- mixed precision
+
+def test_mixed_within_one_percent_of_discretisation_error():
+    """Density advection 16^3 to t = 0.2: the mixed FP32/FP64 result differs
+    from the FP64 result by at most 1% of the FP64 discretisation error."""
+    n = (16, 16, 16)
+    q0 = W.density_advection(n)
+    exact = W.density_advection(n, t=0.2)
+    res = {}
+    for prec in (hgks.HGKS_FP64, hgks.HGKS_MIXED):
+        s = _solver(n, (0, 0, 0), (2, 2, 2), precision=prec)
+        s.set_state(q0)
+        s.step(100, cfl=0.5, t_end=0.2)
+        res[prec], _ = s.get_state()
+        s.close()
+    vol = (2.0 / 16) ** 3
+    disc = np.abs(res[hgks.HGKS_FP64][0] - exact[0]).sum() * vol
+    mix = np.abs(res[hgks.HGKS_MIXED][0] - res[hgks.HGKS_FP64][0]).sum() * vol
+    assert mix <= 0.01 * disc, (mix, disc)
+
+
+def test_mixed_tgv_against_oracle():
+    n = (16, 16, 16)
+    q0, lo, hi = W.taylor_green(n)
+    cfg = oracle.make_cfg(n, lo, hi, mu=1.0 / 1600, Pr=0.72)
+    dt = oracle.cfl_dt(cfg, q0, 0.35)
+    qo, _, _, _ = oracle.step(cfg, q0, 0.0, 10, dt_fixed=dt)
+    s = _solver(n, lo, hi, mu=1.0 / 1600, Pr=0.72, precision=hgks.HGKS_MIXED)
+    s.set_state(q0)
+    s.step(10, dt_fixed=dt)
+    q, _ = s.get_state()
+    s.close()
+    # momentum errors relative to the velocity scale; FP32 flux arithmetic
+    assert max_rel(q, qo) <= 1e-4, max_rel(q, qo)
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_smallest_periodic_grid_parity():
+    n = (2, 2, 2)
+    lo, hi = (0, 0, 0), (1, 1, 1)
+    q0 = W.smooth_random(n, seed=4, lo=lo, hi=hi, amp=0.2)
+    cfg = oracle.make_cfg(n, lo, hi)
+    dt = oracle.cfl_dt(cfg, q0, 0.35)
+    qo, _, _, _ = oracle.step(cfg, q0, 0.0, 2, dt_fixed=dt)
+    s = _solver(n, lo, hi)
+    s.set_state(q0)
+    s.step(2, dt_fixed=dt)
+    q, _ = s.get_state()
+    s.close()
+    assert max_rel(q, qo) <= TOL
+
+
+def test_zero_steps_and_t_end_stop():
+    n = (8, 8, 8)
+    q0 = W.density_advection(n)
+    s = _solver(n, (0, 0, 0), (2, 2, 2))
+    s.set_state(q0, t=0.1)
+    t, done = s.step(0)
+    assert done == 0 and t == 0.1
+    t, done = s.step(1000, cfl=0.5, t_end=0.15)
+    assert abs(t - 0.15) < 1e-15
+    q1, _ = s.get_state()
+    t, done2 = s.step(5, cfl=0.5, t_end=0.15)  # already at t_end: nothing happens
+    q2, _ = s.get_state()
+    assert done2 == done and np.array_equal(q1, q2)
+    with pytest.raises(hgks.HgksError):
+        hgks.hgks_set_option(s.h, "weno_pow", 3)
+    s.close()
+
+
+def test_nonphysical_state_reported():
+    n = (8, 8, 8)
+    q0 = W.density_advection(n)
+    q0[4] = 0.5 * (q0[1] ** 2 + q0[2] ** 2 + q0[3] ** 2) / q0[0] - 1e-3  # negative pressure
+    s = _solver(n, (0, 0, 0), (2, 2, 2))
+    s.set_state(q0)
+    with pytest.raises(hgks.HgksError) as e:
+        s.step(1, dt_fixed=1e-3)
+    assert e.value.code in (hgks.HGKS_E_NONPHYSICAL,)
+    s.close()
+
+
+def test_device_buffers_through_the_abi():
+    import torch
+    n = (12, 10, 8)
+    lo, hi = _box_for(n, 0.1)
+    q0 = W.smooth_random(n, seed=8, lo=lo, hi=hi, amp=0.1)
+    s = _solver(n, lo, hi)
+    qd = torch.from_numpy(q0).cuda()
+    hgks.hgks_set_state(s.h, qd, 0.0)
+    L = torch.zeros_like(qd)
+    dL = torch.zeros_like(qd)
+    hgks.hgks_flux(s.h, 1e-3, L, dL)
+    Lh, dLh = s.flux(1e-3)
+    assert np.array_equal(L.cpu().numpy(), Lh) and np.array_equal(dL.cpu().numpy(), dLh)
+    out = torch.zeros_like(qd)
+    hgks.hgks_get_state(s.h, out)
+    assert np.array_equal(out.cpu().numpy(), q0)
+    s.close()

@@ -126,4 +126,5 @@ def test_table1_density_advection_16():
     exact = W.density_advection(n, t=2.0)
     l1 = _l1(q1[0] - exact[0], (2.0 / 16) ** 3)
     ref = rows[0, 1]
+    print(f"Table 1, 16^3: oracle L1 = {l1:.5e} (paper {ref:.5e}), {done} steps")
     assert ref / 1.5 < l1 < ref * 1.5, (l1, ref)
