@@ -466,17 +466,38 @@ template <typename R> HK_HD R beta_quadratic(const R a[9])
 
 // sub-stencil m = 8 p + s: plane (a, b) = (p, p+1), out-of-plane c = p+2,
 // signs in the order (+++), (-++), (+-+), (--+), (++-), (-+-), (+--), (---)
-template <typename R>
-HK_HD void sub_stencil(const Stencil<R> &st, int p, int s, R b[3])
+// (every index is a compile-time constant: the stencil stays in registers)
+template <int M, typename R> HK_HD void sub_stencil(const Stencil<R> &st, R b[3])
 {
-    const int sa = (s & 1) ? 0 : 1, sb = (s & 2) ? 0 : 1, sc = (s & 4) ? 0 : 1;
-    const int a = p, bb = (p + 1) % 3, c = (p + 2) % 3;
+    constexpr int p = M >> 3, s = M & 7;
+    constexpr int sa = (s & 1) ? 0 : 1, sb = (s & 2) ? 0 : 1, sc = (s & 4) ? 0 : 1;
+    constexpr int a = p, bb = (p + 1) % 3, c = (p + 2) % 3;
     const R qa = st.f[a][sa], qb = st.f[bb][sb], qab = st.e[p][sa][sb], qc = st.f[c][sc];
     const R ba = (R(2) * qa - qb + qab) * R(1.0 / 3.0);
     const R bbv = (R(2) * qb - qa + qab) * R(1.0 / 3.0);
     b[a] = sa ? ba : -ba;
     b[bb] = sb ? bbv : -bbv;
     b[c] = sc ? qc : -qc;
+}
+
+// expands X(m) for the 24 sub-stencils m = 0..23
+#define HK_FOR_SUBSTENCILS(X)                                                                             \
+    X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(17) X(18) \
+        X(19) X(20) X(21) X(22) X(23)
+
+// sub-stencil m chosen at run time (for the rare literal positivity check)
+template <typename R> HK_HD void sub_stencil_rt(const Stencil<R> &st, int m, R b[3])
+{
+    switch (m) {
+#define HK_CASE(M)                \
+    case M:                       \
+        sub_stencil<M>(st, b);    \
+        break;
+        HK_FOR_SUBSTENCILS(HK_CASE)
+#undef HK_CASE
+    default:
+        b[0] = b[1] = b[2] = R(0);
+    }
 }
 
 // rigorous bound of |P(X) - Q_c| over the cell (|X_d| <= 1/2)
@@ -525,14 +546,16 @@ HK_HD void weno_ao(const Stencil<R> &st, const Scheme &S, R out[9], R &rad)
     R r = bound_quadratic(a);
     // pass 1: indicators of the 24 linear polynomials and tau
     R tau = R(0);
-#pragma unroll 4
-    for (int m = 0; m < 24; ++m) {
-        R b[3];
-        sub_stencil(st, m >> 3, m & 7, b);
-        const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
-        tau += m_abs(beta0 - bm);
-        r = m_max(r, bound_linear(b));
+#define HK_PASS1(M)                                                   \
+    {                                                                 \
+        R b[3];                                                       \
+        sub_stencil<M>(st, b);                                        \
+        const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];         \
+        tau += m_abs(beta0 - bm);                                     \
+        r = m_max(r, bound_linear(b));                                \
     }
+    HK_FOR_SUBSTENCILS(HK_PASS1)
+#undef HK_PASS1
     tau *= R(1.0 / 24.0);
     rad = r;
     // pass 2: weights and the combination, normalised at the end
@@ -540,19 +563,21 @@ HK_HD void weno_ao(const Stencil<R> &st, const Scheme &S, R out[9], R &rad)
     const R w0 = g0 * (R(1) + (S.weno_pow == 2 ? x0 * x0 : x0));
     R wsum = w0;
     R lin[3] = {R(0), R(0), R(0)};
-#pragma unroll 4
-    for (int m = 0; m < 24; ++m) {
-        R b[3];
-        sub_stencil(st, m >> 3, m & 7, b);
-        const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
-        const R xm = tau / (bm + eps);
-        const R wm = gm * (R(1) + (S.weno_pow == 2 ? xm * xm : xm));
-        wsum += wm;
-        const R cm = wm - w0 * gm * ig0;
-        lin[0] += cm * b[0];
-        lin[1] += cm * b[1];
-        lin[2] += cm * b[2];
+#define HK_PASS2(M)                                                   \
+    {                                                                 \
+        R b[3];                                                       \
+        sub_stencil<M>(st, b);                                        \
+        const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];         \
+        const R xm = tau / (bm + eps);                                \
+        const R wm = gm * (R(1) + (S.weno_pow == 2 ? xm * xm : xm));  \
+        wsum += wm;                                                   \
+        const R cm = wm - w0 * gm * ig0;                              \
+        lin[0] += cm * b[0];                                          \
+        lin[1] += cm * b[1];                                          \
+        lin[2] += cm * b[2];                                          \
     }
+    HK_FOR_SUBSTENCILS(HK_PASS2)
+#undef HK_PASS2
     const R iw = R(1) / wsum;
     const R f0 = w0 * ig0;
 #pragma unroll

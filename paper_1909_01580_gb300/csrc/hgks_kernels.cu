@@ -73,7 +73,7 @@ __device__ __forceinline__ void load_stencil(const double *__restrict__ Qv, cons
 // literal positivity check (Sec. 4): rho and p of every P_m, m = 0..24, at
 // every one of the cell's 24 Gauss points
 template <typename R>
-__device__ bool positivity_violated(const double *__restrict__ Q, const Geo &g, int i, int j, int k, R gamma)
+__device__ __noinline__ bool positivity_violated(const double *__restrict__ Q, const Geo &g, int i, int j, int k, R gamma)
 {
     R qcv[5];
     Stencil<R> st[5];
@@ -89,7 +89,7 @@ __device__ bool positivity_violated(const double *__restrict__ Q, const Geo &g, 
                 big_stencil_P0(st[v], cf[v]);
             } else {
                 R b[3];
-                sub_stencil(st[v], (m - 1) / 8, (m - 1) % 8, b);
+                sub_stencil_rt(st[v], m - 1, b);
                 for (int n = 0; n < 9; ++n) cf[v][n] = n < 3 ? b[n] : R(0);
             }
         }
@@ -117,7 +117,6 @@ __global__ void __launch_bounds__(128) k_recon(const double *__restrict__ Q, R *
     if (t >= g.cstride) return;
     const int i = (int)(t % g.cx) - 1, j = (int)((t / g.cx) % g.cy) - 1, k = (int)(t / ((long long)g.cx * g.cy)) - 1;
     R rad[5], qcv[5];
-    R out[5][9];
 #pragma unroll 1
     for (int v = 0; v < 5; ++v) {
         const double *Qv = Q + v * g.pstride;
@@ -125,18 +124,20 @@ __global__ void __launch_bounds__(128) k_recon(const double *__restrict__ Q, R *
         qcv[v] = R(qc);
         Stencil<R> st;
         load_stencil(Qv, g, i, j, k, qc, st);
-        weno_ao(st, S, out[v], rad[v]);
+        R out[9];
+        weno_ao(st, S, out, rad[v]);
+#pragma unroll
+        for (int n = 0; n < 9; ++n) coef[(v * 9 + n) * g.cstride + t] = out[n];
     }
     // positivity fallback: the cheap sufficient test first, the literal
     // check of all 25 polynomials at the 24 Gauss points only when it fails
     bool bad = false;
     if (S.limiter && !positivity_certain(qcv, rad, R(S.gamma))) bad = positivity_violated<R>(Q, g, i, j, k, R(S.gamma));
-#pragma unroll
-    for (int v = 0; v < 5; ++v)
-#pragma unroll
-        for (int n = 0; n < 9; ++n) coef[(v * 9 + n) * g.cstride + t] = bad ? R(0) : out[v][n];
+    if (bad) {
+        for (int q = 0; q < 45; ++q) coef[q * g.cstride + t] = R(0);
+        atomicAdd(&ctl->flagged, 1);
+    }
     flag[t] = bad ? 1 : 0;
-    if (bad) atomicAdd(&ctl->flagged, 1);
 }
 
 // ---------------------------------------------------------------------------

@@ -2,9 +2,11 @@
 same seeded inputs: point flux, reconstruction, the operator L and dL/dt,
 10-step runs, full-size sampled cells, and the invariants that hold at any
 size.  Tolerances: FP64 path max relative difference (per variable, max
-|diff| / max |oracle|) <= 1e-11; dL/dt <= 1e-10 because the oracle forms it
-from a 2x2 solve of time integrals that cancels about log10(F/(dt dF))
-digits; mixed path against the FP32 unit round-off."""
+|diff| / max |oracle|) <= 1e-11; dL/dt <= 1e-9 because the oracle forms it
+literally from the 2x2 solve of the time integrals over dt and dt/2, whose
+difference Fh(dt) - 2 Fh(dt/2) cancels: its relative error is about
+4 eps |F| / (|dF| dt), which reaches 3.5e-10 on the octant Riemann data at
+CFL 0.35; mixed path against the FP32 unit round-off."""
 import math
 
 import numpy as np
@@ -18,7 +20,7 @@ from tests._cases import max_rel, random_point_inputs
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-11
-TOL_DT = 1e-10
+TOL_DT = 1e-9
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -158,9 +160,11 @@ def test_ten_steps_density_advection_16():
     assert done_o == 10 and done == 10
     assert abs(t - 0.2) < 1e-14 and abs(t2 - 0.2) < 1e-14
     assert max_rel(q, qo) <= TOL, max_rel(q, qo)
+    # discretisation error against the exact solution (Table 1 reports 0.146
+    # at t = 2 on this mesh; a tenth of the time gives about a tenth of it)
     exact = W.density_advection(n, t=0.2)
     l1 = float(np.abs(q[0] - exact[0]).sum() * (2.0 / 16) ** 3)
-    assert l1 < 5e-3
+    assert 5e-3 < l1 < 3e-2, l1
 
 
 @pytest.mark.parametrize("case,nsteps", [("tgv16", 10), ("octant16", 6), ("smooth_ragged", 10)])
@@ -209,8 +213,17 @@ def test_full_size_sampled_tgv128():
     s.close()
     Ls = L.reshape(5, -1)[:, cells]
     dLs = dL.reshape(5, -1)[:, cells]
-    assert max_rel(Ls, Lo) <= TOL, max_rel(Ls, Lo)
+    # L of a nearly divergence-free low-Mach flow is a small difference of
+    # O(rho c) face fluxes over h = 2 pi/128: its rounding floor relative to
+    # max |L| is about 1e-10, so L is held to 1e-9 and the state increments
+    # dt L and dt^2 dL/dt that a step applies are held to 1e-14 of max |Q|
+    qs = q.reshape(5, -1)[:, cells]
+    assert max_rel(Ls, Lo) <= 1e-9, max_rel(Ls, Lo)
     assert max_rel(dLs, dLo) <= TOL_DT, max_rel(dLs, dLo)
+    for v in range(5):
+        qmax = np.abs(qs[v]).max() if np.abs(qs[v]).max() > 0 else np.abs(qs).max()
+        assert dt * np.abs(Ls[v] - Lo[v]).max() <= 1e-14 * qmax, v
+        assert dt * dt * np.abs(dLs[v] - dLo[v]).max() <= 1e-14 * qmax, v
 
 
 def test_full_size_sampled_octant128_reflective():
@@ -245,6 +258,7 @@ def test_conservation_tgv128_three_steps():
     tot0 = q0.reshape(5, -1).sum(axis=1)
     tot1 = q.reshape(5, -1).sum(axis=1)
     scale = np.abs(q0).reshape(5, -1).sum(axis=1)
+    scale[1:4] = scale[1:4].max()  # W = 0 initially: judge momentum on its common scale
     assert (np.abs(tot1 - tot0) <= 1e-13 * scale).all(), (tot1 - tot0) / scale
 
 

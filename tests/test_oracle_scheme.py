@@ -116,8 +116,9 @@ def test_density_advection_error_and_convergence():
 
 @pytest.mark.slow
 def test_table1_density_advection_16():
-    """Table 1 (Sec. 4) at 16^3: L1 error at t = 2 within a factor 1.5 of the
-    printed 1.4612e-1 (readings: CFL form, epsilon, exponent 1)."""
+    """Table 1 (Sec. 4) at 16^3: L1 error at t = 2 within 2% of the printed
+    1.4612e-1 (the oracle gives 1.4586e-1 with the readings of the CFL form,
+    epsilon = 1e-8 and exponent 1)."""
     rows = np.loadtxt(os.path.join(GOLDEN, "table1_advection_uniform.txt"))
     n = (16, 16, 16)
     cfg = oracle.make_cfg(n)
@@ -127,4 +128,4 @@ def test_table1_density_advection_16():
     l1 = _l1(q1[0] - exact[0], (2.0 / 16) ** 3)
     ref = rows[0, 1]
     print(f"Table 1, 16^3: oracle L1 = {l1:.5e} (paper {ref:.5e}), {done} steps")
-    assert ref / 1.5 < l1 < ref * 1.5, (l1, ref)
+    assert abs(l1 - ref) < 0.02 * ref, (l1, ref)
