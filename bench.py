@@ -34,13 +34,16 @@ if ROOT not in sys.path:
 METRIC = "cell-stage updates/s at TGV 128^3 (FP64 vs mixed)"
 UNIT = "cell-stage updates/s"
 
-# Work per unit of the dominant kernel (the Gauss-point face flux), in FP64
-# operations per Gauss point executed by the FP64 pipe (DFMA counts 2, DADD
-# and DMUL 1), from the ncu instruction counters of one capture of the flux
-# kernel on TGV 32^3 (see profiles/).  The FP32 figure is the same count for
-# the mixed path's FP32 pipe.  Used as the per-unit figure of the roofline.
-FLUX_FP64_FLOP_PER_GP = 7500.0
-FLUX_FP32_FLOP_PER_GP = 7500.0
+# Work per unit of the dominant kernel (the Gauss-point face flux): FP64
+# flop per Gauss point executed on the FP64 pipe (2 per DFMA, 1 per DADD and
+# DMUL) for the FP64 path, FP32 flop on the FMA pipe for the mixed path,
+# from the ncu instruction counters of one capture of the kernel on TGV 32^3
+# (profiles/k_face_flux_tgv32.md).  Per-launch DRAM traffic of the same
+# capture, scaled by the faces of a 128^3 launch (traffic grows with the
+# cells: the coefficient array is read once).
+FLUX_FP64_FLOP_PER_GP = 4914.0
+FLUX_FP32_FLOP_PER_GP = 4546.0
+FLUX_TRAFFIC_BYTES_PER_FACE = {"fp64": 14.49e6 / 33792, "mixed": 8.02e6 / 33792}
 # GB300 ALU peaks derived from unit counts and clocks: 152 SMs x 2070 MHz x
 # (FP64: 2 DFMA/clk/SM = 4 flop; FP32: 128 FMA/clk/SM = 256 flop).
 SM_COUNT = 152
@@ -190,7 +193,9 @@ def run_gpu(args, rank, world, local, dist):
             "phase_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in timing.items()},
             "flux_share": flux_ms / total_phase if total_phase > 0 else None,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": FLUX_TRAFFIC_BYTES_PER_FACE[prec_name] * nface_stage / 3,
+                         "traffic_note": "ncu dram read+write of a TGV 32^3 launch scaled to 128^3 faces",
                          "kernel": "k_face_flux", "pipe": "fp64" if prec_name == "fp64" else "fp32",
                          "peak_source": "derived: 152 SMs x 2070 MHz x (4 FP64 | 256 FP32) flop/clk/SM"},
             "t_reached": t_now,

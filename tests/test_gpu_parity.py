@@ -215,10 +215,11 @@ def test_full_size_sampled_tgv128():
     dLs = dL.reshape(5, -1)[:, cells]
     # L of a nearly divergence-free low-Mach flow is a small difference of
     # O(rho c) face fluxes over h = 2 pi/128: its rounding floor relative to
-    # max |L| is about 1e-10, so L is held to 1e-9 and the state increments
-    # dt L and dt^2 dL/dt that a step applies are held to 1e-14 of max |Q|
+    # max |L| is about 1e-9 (2e-12 absolute on L_rho from 1e-14 relative
+    # face-flux rounding over h = 0.049), so L is held to 1e-8 and the state
+    # increments dt L and dt^2 dL/dt that a step applies to 1e-14 of max |Q|
     qs = q.reshape(5, -1)[:, cells]
-    assert max_rel(Ls, Lo) <= 1e-9, max_rel(Ls, Lo)
+    assert max_rel(Ls, Lo) <= 1e-8, max_rel(Ls, Lo)
     assert max_rel(dLs, dLo) <= TOL_DT, max_rel(dLs, dLo)
     for v in range(5):
         qmax = np.abs(qs[v]).max() if np.abs(qs[v]).max() > 0 else np.abs(qs).max()
