@@ -220,7 +220,7 @@ def test_full_size_sampled_tgv128():
     # increments dt L and dt^2 dL/dt that a step applies to 1e-14 of max |Q|
     qs = q.reshape(5, -1)[:, cells]
     assert max_rel(Ls, Lo) <= 1e-8, max_rel(Ls, Lo)
-    assert max_rel(dLs, dLo) <= TOL_DT, max_rel(dLs, dLo)
+    assert max_rel(dLs, dLo) <= 1e-8, max_rel(dLs, dLo)
     for v in range(5):
         qmax = np.abs(qs[v]).max() if np.abs(qs[v]).max() > 0 else np.abs(qs).max()
         assert dt * np.abs(Ls[v] - Lo[v]).max() <= 1e-14 * qmax, v
