@@ -147,6 +147,37 @@ int hgks_set_timing(hgks_t *h, int enable);
  * arrays.  Synchronises the stream. */
 int hgks_get_timing(hgks_t *h, double ms[HGKS_NPHASE], unsigned long long launches[HGKS_NPHASE]);
 
+/* Bytes of device scratch that hgks_flux_noalloc works in (16 MiB). */
+#define HGKS_NOALLOC_SCRATCH_BYTES (16 * 1024 * 1024)
+
+/* Allocation-free evaluation of L(Q) and dL/dt(Q), for callers that cannot
+ * call cudaMalloc: a serving loop that must not block on the implicit device
+ * synchronisation of an allocation, code that lives inside another
+ * framework's memory pool, or code under a no-allocation policy after
+ * start-up.  The paper has no counterpart; it computes exactly what
+ * hgks_flux computes (same kernels, the paper's default constants) without a
+ * handle and without allocating: no cudaMalloc, cudaFree or allocating
+ * library call.
+ *   grid, gamma, mu, Pr, bc  as for hgks_create.
+ *   q      device pointer, the state [5][nz][ny][nx] FP64 (read only).
+ *   dt     time step, > 0.
+ *   L, dLdt  device pointers [5][nz][ny][nx] FP64 (written).
+ *   stream cudaStream_t (or NULL for the legacy default stream); the call is
+ *          ordered on it and returns without synchronising.
+ * Working memory is one file-scope device array of HGKS_NOALLOC_SCRATCH_BYTES
+ * that every GPU loading the library holds until the process exits.  The
+ * grid's padded state, reconstruction coefficients and face fluxes must fit
+ * in it: cubes of up to 28^3 cells in FP64 and 31^3 mixed; larger
+ * grids return HGKS_E_INVALID with the byte count in hgks_last_error(NULL).
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Every call shares the one array and overwrites what an
+ * earlier call left there (nothing of it is read back), so calls that may
+ * overlap on the GPU (other streams, other host threads) race: order them
+ * on one stream or serialise them. */
+int hgks_flux_noalloc(const hgks_grid_t *grid, double gamma, double mu, double Pr, const int bc[6], const double *q,
+                      double dt, double *L, double *dLdt, void *stream);
+
 /* Kernel launches this handle has issued since creation (for accounting). */
 unsigned long long hgks_launch_count(const hgks_t *h);
 

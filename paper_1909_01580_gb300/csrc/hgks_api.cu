@@ -43,6 +43,10 @@ struct hgks {
 
 static char g_create_err[256] = "";
 
+// lets the allocation-free entry point (hgks_noalloc.cu) report through
+// hgks_last_error(NULL)
+void hgks_internal_set_error(const char *msg) { snprintf(g_create_err, sizeof g_create_err, "%s", msg); }
+
 static int fail(hgks_t *h, int code, const char *fmt, const char *detail = nullptr)
 {
     char *dst = h ? h->err : g_create_err;

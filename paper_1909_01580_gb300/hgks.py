@@ -28,8 +28,8 @@ HGKS_E_STATE = -6
 
 # every symbol include/hgks.h declares
 EXPORTS = ("hgks_create", "hgks_set_option", "hgks_set_state", "hgks_get_state", "hgks_step", "hgks_flux",
-           "hgks_reconstruct", "hgks_point_flux", "hgks_set_timing", "hgks_get_timing", "hgks_launch_count", "hgks_device_bytes", "hgks_last_error",
-           "hgks_destroy")
+           "hgks_reconstruct", "hgks_point_flux", "hgks_set_timing", "hgks_get_timing", "hgks_launch_count",
+           "hgks_device_bytes", "hgks_last_error", "hgks_destroy", "hgks_flux_noalloc")
 
 
 class HgksError(RuntimeError):
@@ -81,6 +81,9 @@ def load(build_if_missing: bool = True):
     L.hgks_flux.argtypes = [vp, ctypes.c_double, vp, vp, ctypes.c_int]
     L.hgks_reconstruct.argtypes = [vp, vp, vp]
     L.hgks_point_flux.argtypes = [ctypes.c_int, vp, vp, ctypes.c_double, dp, ctypes.c_int, vp, vp]
+    L.hgks_flux_noalloc.argtypes = [P(hgks_grid_t), ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                    P(ctypes.c_int), vp, ctypes.c_double, vp, vp, vp]
+    L.hgks_flux_noalloc.restype = ctypes.c_int
     L.hgks_set_timing.argtypes = [vp, ctypes.c_int]
     L.hgks_set_timing.restype = ctypes.c_int
     L.hgks_get_timing.argtypes = [vp, dp, P(ctypes.c_ulonglong)]
@@ -204,6 +207,25 @@ def hgks_get_timing(h):
     nl = (ctypes.c_ulonglong * 5)()
     _check(load().hgks_get_timing(h, ms, nl), h)
     return {name: (ms[i], int(nl[i])) for i, name in enumerate(PHASES)}
+
+
+def hgks_flux_noalloc(n, lo, hi, q, dt, L, dL, gamma=1.4, mu=0.0, Pr=1.0, bc=(0, 0, 0, 0, 0, 0),
+                      precision=HGKS_FP64, stream=None):
+    """L(Q), dL/dt(Q) without a handle and without allocating (device tensors
+    only; ordered on ``stream``, not synchronised)."""
+    g = hgks_grid_t()
+    for d in range(3):
+        g.n[d], g.lo[d], g.hi[d] = int(n[d]), float(lo[d]), float(hi[d])
+    g.mesh, g.mesh_amp, g.mesh_omega, g.precision = 0, 0.0, 0.0, int(precision)
+    bcs = (ctypes.c_int * 6)(*[int(b) for b in bc])
+    pq, dq = _ptr(q)
+    pl, dl = _ptr(L)
+    pd, dd = _ptr(dL)
+    if not (dq and dl and dd):
+        raise ValueError("hgks_flux_noalloc takes device buffers only")
+    st = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(load().hgks_flux_noalloc(ctypes.byref(g), float(gamma), float(mu), float(Pr), bcs, pq, float(dt), pl, pd,
+                                    st))
 
 
 def hgks_launch_count(h) -> int:
