@@ -23,7 +23,7 @@ struct hgks {
     bool own_stream;
     int device;
     double *Qn, *Qs, *Wacc;      // padded Q^n, padded Q*, accumulator / staging [5][ncell]
-    void *coef;                  // [45][cstride] in the working precision
+    void *coef;                  // [NCOEF][cstride] in the working precision
     unsigned char *flag;         // [cstride]
     double *F[3];                // face fluxes [10][nface_d]
     Ctl *ctl;                    // device control block
@@ -217,7 +217,7 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
     }
     const size_t rsz = grid->precision == HGKS_MIXED ? sizeof(float) : sizeof(double);
     size_t sizes[] = {5 * g.pstride * sizeof(double), 5 * g.pstride * sizeof(double), 5 * g.ncell * sizeof(double),
-                      45 * g.cstride * rsz, (size_t)g.cstride};
+                      hk::NCOEF * g.cstride * rsz, (size_t)g.cstride};
     void **ptrs[] = {(void **)&h->Qn, (void **)&h->Qs, (void **)&h->Wacc, &h->coef, (void **)&h->flag};
     bool ok = true;
     for (int i = 0; i < 5 && ok; ++i) {
@@ -337,7 +337,7 @@ static int stage_fluxes(hgks_t *h, double *Q)
             hk::launch_recon<float>(Q, c, h->flag, g, h->S, h->ctl, s);
         }
         PhaseTimer t(h, HGKS_PHASE_FLUX, 3);
-        for (int d = 0; d < 3; ++d) hk::launch_flux<float>(d, Q, c, h->F[d], g, h->S, h->ctl, s);
+        for (int d = 0; d < 3; ++d) hk::launch_flux<float>(d, c, h->F[d], g, h->S, h->ctl, s);
     } else {
         double *c = (double *)h->coef;
         {
@@ -345,7 +345,7 @@ static int stage_fluxes(hgks_t *h, double *Q)
             hk::launch_recon<double>(Q, c, h->flag, g, h->S, h->ctl, s);
         }
         PhaseTimer t(h, HGKS_PHASE_FLUX, 3);
-        for (int d = 0; d < 3; ++d) hk::launch_flux<double>(d, Q, c, h->F[d], g, h->S, h->ctl, s);
+        for (int d = 0; d < 3; ++d) hk::launch_flux<double>(d, c, h->F[d], g, h->S, h->ctl, s);
     }
     return check_launch(h, 5);
 }

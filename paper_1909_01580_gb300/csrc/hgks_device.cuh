@@ -65,6 +65,12 @@ HK_HD long long cidx(const Geo &g, int i, int j, int k)
     return ((long long)(k + 1) * g.cy + (j + 1)) * g.cx + (i + 1);
 }
 
+// Reconstruction storage per cell, in the working precision: for each of
+// the 5 variables the cell average Q_c (slot 0) and the 9 coefficients of
+// P~ - Q_c (slots 1..9); term stride Geo::cstride.
+constexpr int NCOEF = 50;
+HK_HD int coef_slot(int v, int n) { return v * 10 + n; }
+
 // Per-handle device control block: time, step and status.
 struct Ctl {
     double t, dt;

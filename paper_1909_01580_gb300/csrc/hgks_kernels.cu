@@ -127,14 +127,17 @@ __global__ void __launch_bounds__(128) k_recon(const double *__restrict__ Q, R *
         R out[9];
         weno_ao(st, S, out, rad[v]);
 #pragma unroll
-        for (int n = 0; n < 9; ++n) coef[(v * 9 + n) * g.cstride + t] = out[n];
+        coef[coef_slot(v, 0) * g.cstride + t] = R(qc);
+#pragma unroll
+        for (int n = 0; n < 9; ++n) coef[coef_slot(v, 1 + n) * g.cstride + t] = out[n];
     }
     // positivity fallback: the cheap sufficient test first, the literal
     // check of all 25 polynomials at the 24 Gauss points only when it fails
     bool bad = false;
     if (S.limiter && !positivity_certain(qcv, rad, R(S.gamma))) bad = positivity_violated<R>(Q, g, i, j, k, R(S.gamma));
     if (bad) {
-        for (int q = 0; q < 45; ++q) coef[q * g.cstride + t] = R(0);
+        for (int v = 0; v < 5; ++v)
+            for (int n = 1; n < 10; ++n) coef[coef_slot(v, n) * g.cstride + t] = R(0);
         atomicAdd(&ctl->flagged, 1);
     }
     flag[t] = bad ? 1 : 0;
@@ -148,8 +151,8 @@ __global__ void __launch_bounds__(128) k_recon(const double *__restrict__ Q, R *
 // the face-averaged flux per unit area.
 // ---------------------------------------------------------------------------
 template <typename R, int D>
-__device__ __forceinline__ void eval_side(const double *__restrict__ Q, const R *__restrict__ coef, const Geo &g,
-                                          long long ci, long long qi, R xd, R xa, R xb, R W[5], R dW[3][5])
+__device__ __forceinline__ void eval_side(const R *__restrict__ coef, const Geo &g, long long ci, R xd, R xa, R xb,
+                                          R W[5], R dW[3][5])
 {
     R X[3];
     X[D] = xd;
@@ -161,10 +164,10 @@ __device__ __forceinline__ void eval_side(const double *__restrict__ Q, const R 
     for (int v = 0; v < 5; ++v) {
         R c[9];
 #pragma unroll
-        for (int n = 0; n < 9; ++n) c[n] = coef[(v * 9 + n) * g.cstride + ci];
+        for (int n = 0; n < 9; ++n) c[n] = coef[coef_slot(v, 1 + n) * g.cstride + ci];
         R s;
         poly_value_grad(c, X, ih, s, grad[v]);
-        val[v] = R(Q[v * g.pstride + qi] + double(s));
+        val[v] = coef[coef_slot(v, 0) * g.cstride + ci] + s;
     }
     // local frame: local axis l is global axis (D + l) % 3
     W[0] = val[0];
@@ -182,8 +185,8 @@ __device__ __forceinline__ void eval_side(const double *__restrict__ Q, const R 
 }
 
 template <typename R, int D>
-__global__ void __launch_bounds__(128) k_face_flux(const double *__restrict__ Q, const R *__restrict__ coef,
-                                                   double *__restrict__ Fout, Geo g, Scheme S, Ctl *ctl)
+__global__ void __launch_bounds__(128) k_face_flux(const R *__restrict__ coef, double *__restrict__ Fout, Geo g,
+                                                   Scheme S, Ctl *ctl)
 {
     if (!ctl->active) return;
     const double dt = ctl->dt;
@@ -200,20 +203,21 @@ __global__ void __launch_bounds__(128) k_face_flux(const double *__restrict__ Q,
     const R xa = (gp & 2) ? R(GAUSS_S) : R(-GAUSS_S);
     const R xb = (gp & 1) ? R(GAUSS_S) : R(-GAUSS_S);
     R Wl[5], dWl[3][5], Wr[5], dWr[3][5];
-    eval_side<R, D>(Q, coef, g, cidx(g, il, jl, kl), pidx(g, il, jl, kl), R(0.5), xa, xb, Wl, dWl);
-    eval_side<R, D>(Q, coef, g, cidx(g, i, j, k), pidx(g, i, j, k), R(-0.5), xa, xb, Wr, dWr);
+    eval_side<R, D>(coef, g, cidx(g, il, jl, kl), R(0.5), xa, xb, Wl, dWl);
+    eval_side<R, D>(coef, g, cidx(g, i, j, k), R(-0.5), xa, xb, Wr, dWr);
     R F[5], dF[5];
     gks_flux<R>(Wl, dWl, Wr, dWr, S, R(dt), F, dF);
-    // back to the global frame, Gauss weight 1/4, sum of the 4 lanes
-    double f[10];
-    f[0] = 0.25 * double(F[0]);
-    f[4] = 0.25 * double(F[4]);
-    f[5] = 0.25 * double(dF[0]);
-    f[9] = 0.25 * double(dF[4]);
+    // back to the global frame, Gauss weight 1/4, sum of the 4 lanes in the
+    // working precision; the face value is stored in FP64
+    R f[10];
+    f[0] = R(0.25) * F[0];
+    f[4] = R(0.25) * F[4];
+    f[5] = R(0.25) * dF[0];
+    f[9] = R(0.25) * dF[4];
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
-        f[1 + (D + l) % 3] = 0.25 * double(F[1 + l]);
-        f[6 + (D + l) % 3] = 0.25 * double(dF[1 + l]);
+        f[1 + (D + l) % 3] = R(0.25) * F[1 + l];
+        f[6 + (D + l) % 3] = R(0.25) * dF[1 + l];
     }
 #pragma unroll
     for (int q = 0; q < 10; ++q) {
@@ -222,7 +226,7 @@ __global__ void __launch_bounds__(128) k_face_flux(const double *__restrict__ Q,
     }
     if (valid && gp == 0) {
 #pragma unroll
-        for (int q = 0; q < 10; ++q) Fout[q * nface + face] = f[q];
+        for (int q = 0; q < 10; ++q) Fout[q * nface + face] = double(f[q]);
     }
 }
 
@@ -395,7 +399,8 @@ __global__ void k_export_coef(const R *__restrict__ coef, const unsigned char *_
     if (t >= g.ncell) return;
     const int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / ((long long)g.nx * g.ny));
     const long long ci = cidx(g, i, j, k);
-    for (int q = 0; q < 45; ++q) out[t * 45 + q] = double(coef[q * g.cstride + ci]);
+    for (int v = 0; v < 5; ++v)
+        for (int n = 0; n < 9; ++n) out[t * 45 + v * 9 + n] = double(coef[coef_slot(v, 1 + n) * g.cstride + ci]);
     if (oflag) oflag[t] = flag[ci];
 }
 
@@ -463,14 +468,13 @@ void launch_recon(const double *Q, R *coef, unsigned char *flag, const Geo &g, c
 }
 
 template <typename R>
-void launch_flux(int axis, const double *Q, const R *coef, double *F, const Geo &g, const Scheme &S, Ctl *ctl,
-                 cudaStream_t s)
+void launch_flux(int axis, const R *coef, double *F, const Geo &g, const Scheme &S, Ctl *ctl, cudaStream_t s)
 {
     const long long nface = (long long)(g.nx + (axis == 0)) * (g.ny + (axis == 1)) * (g.nz + (axis == 2));
     const unsigned nb = blocks_for(4 * nface, 128);
-    if (axis == 0) k_face_flux<R, 0><<<nb, 128, 0, s>>>(Q, coef, F, g, S, ctl);
-    else if (axis == 1) k_face_flux<R, 1><<<nb, 128, 0, s>>>(Q, coef, F, g, S, ctl);
-    else k_face_flux<R, 2><<<nb, 128, 0, s>>>(Q, coef, F, g, S, ctl);
+    if (axis == 0) k_face_flux<R, 0><<<nb, 128, 0, s>>>(coef, F, g, S, ctl);
+    else if (axis == 1) k_face_flux<R, 1><<<nb, 128, 0, s>>>(coef, F, g, S, ctl);
+    else k_face_flux<R, 2><<<nb, 128, 0, s>>>(coef, F, g, S, ctl);
 }
 
 void launch_update(int stage, double *Qn, double *Qs, double *Wacc, const double *Fx, const double *Fy,
@@ -529,10 +533,8 @@ template void launch_recon<double>(const double *, double *, unsigned char *, co
                                    cudaStream_t);
 template void launch_recon<float>(const double *, float *, unsigned char *, const Geo &, const Scheme &, Ctl *,
                                   cudaStream_t);
-template void launch_flux<double>(int, const double *, const double *, double *, const Geo &, const Scheme &, Ctl *,
-                                  cudaStream_t);
-template void launch_flux<float>(int, const double *, const float *, double *, const Geo &, const Scheme &, Ctl *,
-                                 cudaStream_t);
+template void launch_flux<double>(int, const double *, double *, const Geo &, const Scheme &, Ctl *, cudaStream_t);
+template void launch_flux<float>(int, const float *, double *, const Geo &, const Scheme &, Ctl *, cudaStream_t);
 template void launch_export_coef<double>(const double *, const unsigned char *, const Geo &, double *, int *,
                                          cudaStream_t);
 template void launch_export_coef<float>(const float *, const unsigned char *, const Geo &, double *, int *,

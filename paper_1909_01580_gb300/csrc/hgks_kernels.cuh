@@ -9,8 +9,7 @@ template <typename R>
 void launch_recon(const double *Q, R *coef, unsigned char *flag, const Geo &g, const Scheme &S, Ctl *ctl,
                   cudaStream_t s);
 template <typename R>
-void launch_flux(int axis, const double *Q, const R *coef, double *F, const Geo &g, const Scheme &S, Ctl *ctl,
-                 cudaStream_t s);
+void launch_flux(int axis, const R *coef, double *F, const Geo &g, const Scheme &S, Ctl *ctl, cudaStream_t s);
 void launch_update(int stage, double *Qn, double *Qs, double *Wacc, const double *Fx, const double *Fy,
                    const double *Fz, const Geo &g, double gamma, Ctl *ctl, cudaStream_t s);
 void launch_residual(const double *Fx, const double *Fy, const double *Fz, const Geo &g, double *L, double *dL,

@@ -138,7 +138,7 @@ extern "C" int hgks_flux_noalloc(const hgks_grid_t *grid, double gamma, double m
     size_t off_ctl = 0;
     size_t off_q = off_ctl + round256(sizeof(Ctl));
     size_t off_coef = off_q + round256(5 * (size_t)g.pstride * sizeof(double));
-    size_t off_flag = off_coef + round256(45 * (size_t)g.cstride * rsz);
+    size_t off_flag = off_coef + round256(hk::NCOEF * (size_t)g.cstride * rsz);
     size_t off_f[3];
     size_t end = off_flag + round256((size_t)g.cstride);
     for (int d = 0; d < 3; ++d) {
@@ -176,10 +176,10 @@ extern "C" int hgks_flux_noalloc(const hgks_grid_t *grid, double gamma, double m
     hk::launch_halo(Q, g, s);
     if (mixed) {
         hk::launch_recon<float>(Q, (float *)coef, flag, g, S, ctl, s);
-        for (int d = 0; d < 3; ++d) hk::launch_flux<float>(d, Q, (const float *)coef, F[d], g, S, ctl, s);
+        for (int d = 0; d < 3; ++d) hk::launch_flux<float>(d, (const float *)coef, F[d], g, S, ctl, s);
     } else {
         hk::launch_recon<double>(Q, (double *)coef, flag, g, S, ctl, s);
-        for (int d = 0; d < 3; ++d) hk::launch_flux<double>(d, Q, (const double *)coef, F[d], g, S, ctl, s);
+        for (int d = 0; d < 3; ++d) hk::launch_flux<double>(d, (const double *)coef, F[d], g, S, ctl, s);
     }
     hk::launch_residual(F[0], F[1], F[2], g, L, dLdt, s);
     cudaError_t e = cudaGetLastError();
