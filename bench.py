@@ -224,6 +224,37 @@ def run_gpu(args, rank, world, local, dist):
     return results
 
 
+def serving_run(count=16, sizes=(24, 32, 48), steps=(20, 40), seed=0, load=1.25, precisions=("fp64", "mixed"),
+                arena_gb=4.0):
+    """Serving workload: seeded requests (density advection / TGV 50:50,
+    uniform sizes, Mach U[0.05, 0.3], Re U[400, 3200]).  One-at-a-time FP64
+    solves give the service times; arrivals are Poisson at `load` times that
+    sequential capacity; the continuous-batching loop then serves the same
+    arrivals in real time with an arena of arena_gb GB (admission by HBM
+    footprint) for each precision."""
+    from paper_1909_01580_gb300 import hgks, serving
+    reqs = serving.request_stream(count=count, seed=seed, sizes=sizes, steps=steps)
+    fifo = serving.serve_fifo(reqs, precision=hgks.HGKS_FP64)
+    rate = load * count / fifo["busy"]
+    serving.poisson_arrivals(reqs, rate, seed=seed)
+    base = serving.fifo_latencies(reqs, fifo["service"])
+    out = {"requests": count, "sizes": list(sizes), "steps": list(steps), "seed": seed,
+           "arrival_rate_per_s": rate, "load_vs_sequential_fp64": load, "arena_gb": arena_gb,
+           "fifo_fp64": serving.summary("fifo_fp64", base, reqs)}
+    cells = sum(2 * r.cells * r.steps_target for r in reqs)
+    for name in precisions:
+        prec = hgks.HGKS_FP64 if name == "fp64" else hgks.HGKS_MIXED
+        res = serving.serve_batched(reqs, precision=prec, arena_bytes=int(arena_gb * (1 << 30)),
+                                    max_instances=64, steps_per_poll=4, keep_results=False)
+        s = serving.summary(f"batched_{name}", res, reqs)
+        s["max_resident"] = res["max_resident"]
+        s["gpu_launches"] = res["launches"]
+        s["cell_stage_updates_per_s"] = res["cell_stages"] / res["makespan"]
+        out[f"batched_{name}"] = s
+    out["approx_cell_stages"] = cells
+    return out
+
+
 def cpu_baseline(n, steps_budget_s=12.0, block=(32, 32, 16)):
     """The oracle as it stands on the host cores: one operator evaluation (one
     stage's reconstruction and face fluxes) over a contiguous block of cells of
@@ -286,8 +317,21 @@ def main():
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the small serving run of the default line")
+    ap.add_argument("--serving", action="store_true",
+                    help="only the serving benchmark: 64 requests on 24^3..96^3, printed as its own line")
+    ap.add_argument("--serving-steps-max", type=int, default=80)
     args = ap.parse_args()
     rank, world, local = _dist_env()
+
+    if args.serving:
+        if rank == 0:
+            import torch
+            torch.cuda.set_device(local)
+            res = serving_run(count=64, sizes=(24, 32, 48, 64, 96), steps=(20, args.serving_steps_max), seed=0)
+            print(json.dumps({"metric": "serving time-to-solution p50/p99 (continuous batching vs one at a time)",
+                              "unit": "s", "higher_is_better": False, "data": "synthetic", **res}))
+        return
 
     if args.impl == "reference":
         if rank == 0:
@@ -331,6 +375,8 @@ def main():
         if "e2e" in main_r:
             line["e2e"] = main_r["e2e"]
             line["mixed"]["e2e"] = res["mixed"].get("e2e")
+        if not args.no_serving and world == 1:
+            line["serving"] = serving_run()
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(args.n)
         print(json.dumps(line))

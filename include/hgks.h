@@ -95,7 +95,8 @@ int hgks_get_state(hgks_t *h, double *q, int on_device, double *t);
  *   Q^{n+1} = Q^n + dt L(Q^n) + dt^2/6 (dL/dt(Q^n) + 2 dL/dt(Q*)).
  * dt_fixed > 0 fixes dt; otherwise dt = cfl * min_cells h/(|U| + c),
  * reduced on the device and clipped so that t does not pass t_end; steps
- * after t reaches t_end do nothing.  *t_out and *steps_done (either may be
+ * after t reaches t_end do nothing (with a finite t_end the call checks every
+ * 16 steps and stops issuing them).  *t_out and *steps_done (either may be
  * NULL) receive the time reached and the steps taken; passing them
  * synchronises the stream.  Returns HGKS_E_NONPHYSICAL if a step produced
  * NaN or non-positive density or pressure. */
@@ -146,6 +147,76 @@ int hgks_set_timing(hgks_t *h, int enable);
  * since the last hgks_set_timing.  ms and launches: [HGKS_NPHASE] host
  * arrays.  Synchronises the stream. */
 int hgks_get_timing(hgks_t *h, double ms[HGKS_NPHASE], unsigned long long launches[HGKS_NPHASE]);
+
+/* ---------------------------------------------------------------------------
+ * Batched execution (system layer around the paper's method; the paper has
+ * no counterpart).  Many instances of different grid sizes and flow
+ * parameters advance together: each phase of a stage (CFL reduction, ghost
+ * fill, reconstruction, the three face-flux directions, update) is one
+ * persistent launch over a tile table that spans every resident instance,
+ * and a whole step is one CUDA graph launch.  Each instance takes its own dt
+ * from its own CFL reduction and stops at its own end time; an instance's
+ * arithmetic is the same alone and in a batch.  Instances live in one device
+ * arena allocated at creation: adding and removing them allocates nothing
+ * on the device.
+ * ------------------------------------------------------------------------- */
+typedef struct hgks_batch hgks_batch_t;
+
+/* Number of tuning parameters: [0] tile schedule (0 slot order, 1 largest
+ * instance first, 2 round robin), [1..5] tile size in multiples of the
+ * block for the CFL, ghost, reconstruction, flux and update phases,
+ * [6..10] persistent blocks per SM for the same phases. */
+#define HGKS_TUNE_NPARAM 11
+
+/* Create a batch of at most max_instances instances with arena_bytes of
+ * device memory for them (one allocation, here), all in one precision. */
+int hgks_batch_create(int precision, unsigned long long arena_bytes, int max_instances, void *stream,
+                      hgks_batch_t **out);
+
+/* Arena bytes one instance of this grid needs (0 for an invalid grid):
+ * the admission test of a serving loop. */
+unsigned long long hgks_batch_footprint(const hgks_grid_t *grid);
+
+/* Admit an instance: grid/gamma/mu/Pr/bc as for hgks_create (grid->precision
+ * must equal the batch's), q its initial state ([5][nz][ny][nx] FP64 host),
+ * t0 its time, t_end its end time, cfl its CFL number.  *slot receives its
+ * slot.  HGKS_E_NOMEM when no slot or not enough free arena is left.
+ * Synchronises the batch stream. */
+int hgks_batch_add(hgks_batch_t *b, const hgks_grid_t *grid, double gamma, double mu, double Pr, const int bc[6],
+                   const double *q, double t0, double t_end, double cfl, int *slot);
+
+/* Retire the instance in slot and return its arena memory. */
+int hgks_batch_remove(hgks_batch_t *b, int slot);
+
+/* Advance every resident instance nsteps two-stage steps (instances at
+ * their end time do nothing).  Asynchronous: graph launches on the stream. */
+int hgks_batch_step(hgks_batch_t *b, int nsteps);
+
+/* Per slot (arrays of max_instances, any may be NULL): time, steps taken,
+ * state 0 free, 1 running, 2 reached its end time, 3 nonphysical.
+ * Synchronises the batch stream. */
+int hgks_batch_poll(hgks_batch_t *b, double *t, int *steps, int *state);
+
+/* Copy the state of the instance in slot to q ([5][nz][ny][nx] FP64 host). */
+int hgks_batch_get_state(hgks_batch_t *b, int slot, double *q);
+
+/* Autotuner: coordinate search over the tuning parameters, timing
+ * steps_per_trial graph-launched steps of the current batch per candidate
+ * (this advances the resident instances), keeps the fastest and returns it
+ * in params_out (may be NULL). */
+int hgks_batch_tune(hgks_batch_t *b, int steps_per_trial, int params_out[HGKS_TUNE_NPARAM]);
+
+/* Set or read the tuning parameters (see HGKS_TUNE_NPARAM). */
+int hgks_batch_set_tuning(hgks_batch_t *b, const int params[HGKS_TUNE_NPARAM]);
+int hgks_batch_get_tuning(const hgks_batch_t *b, int params[HGKS_TUNE_NPARAM]);
+
+/* Kernel launches issued by the batch (graph nodes counted per step). */
+unsigned long long hgks_batch_launch_count(const hgks_batch_t *b);
+
+/* One-line reason for the last failure on b (or on creation when NULL). */
+const char *hgks_batch_last_error(const hgks_batch_t *b);
+
+void hgks_batch_destroy(hgks_batch_t *b);
 
 /* Bytes of device scratch that hgks_flux_noalloc works in (16 MiB). */
 #define HGKS_NOALLOC_SCRATCH_BYTES (16 * 1024 * 1024)

@@ -244,7 +244,7 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
     cudaMemsetAsync(h->Wacc, 0, sizes[2], h->stream);
     cudaMemsetAsync(h->coef, 0, sizes[3], h->stream);
     cudaMemsetAsync(h->flag, 0, sizes[4], h->stream);
-    hk::launch_set_ctl(h->ctl, 0.0, 0.0, 0, h->stream);
+    hk::launch_init_ctl(h->ctl, 0.0, h->stream);
     if (check_launch(h, 1) != HGKS_OK || cudaStreamSynchronize(h->stream) != cudaSuccess) {
         cudaGetLastError();
         free_all(h);
@@ -292,7 +292,7 @@ extern "C" int hgks_set_state(hgks_t *h, const double *q, int on_device, double 
         src = h->Wacc;
     }
     hk::launch_scatter(src, h->Qn, g, h->stream);
-    hk::launch_set_ctl(h->ctl, t, 0.0, 0, h->stream);
+    hk::launch_init_ctl(h->ctl, t, h->stream);
     int rc = check_launch(h, 2);
     if (rc) return rc;
     if (!on_device) CUDA_OK(h, cudaStreamSynchronize(h->stream));
@@ -382,6 +382,13 @@ extern "C" int hgks_step(hgks_t *h, int nsteps, double cfl, double dt_fixed, dou
             hk::launch_update(2, h->Qn, h->Qs, h->Wacc, h->F[0], h->F[1], h->F[2], g, h->S.gamma, h->ctl, s);
         }
         if ((rc = check_launch(h, 1))) return rc;
+        // with a finite end time, look every 16 steps whether it is reached
+        // and stop issuing steps that would do nothing
+        if (!(dt_fixed > 0.0) && isfinite(t_end) && (n + 1) % 16 == 0 && n + 1 < nsteps) {
+            CUDA_OK(h, cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+            CUDA_OK(h, cudaStreamSynchronize(s));
+            if (h->ctl_host->t >= t_end) break;
+        }
     }
     if (t_out || steps_done) {
         CUDA_OK(h, cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));

@@ -1,0 +1,361 @@
+// Per-item bodies of the stage sweep (one cell, one padded cell or one
+// Gauss point per call), shared by the single-instance kernels
+// (hgks_kernels.cu) and the batched persistent kernels (hgks_batch.cu) so
+// that an instance computes the same arithmetic alone and in a batch.
+#pragma once
+#include <limits.h>
+
+#include "hgks_device.cuh"
+
+namespace hk {
+
+// the 2-point Gauss-Legendre node on [-1/2, 1/2]
+#define GAUSS_S 0.28867513459481288225
+
+// ---------------------------------------------------------------------------
+// ghost cells: periodic wrap or reflective mirror (normal momentum negated),
+// width 2 including edge and corner ghosts; every ghost reads its interior
+// source directly, so one pass fills all of them.  t: padded linear index.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void halo_item(double *__restrict__ Q, const Geo &g, long long t)
+{
+    if (t >= g.pstride) return;
+    const int ip = (int)(t % g.px), jp = (int)((t / g.px) % g.py), kp = (int)(t / ((long long)g.px * g.py));
+    const int idx[3] = {ip - 2, jp - 2, kp - 2};
+    const int n[3] = {g.nx, g.ny, g.nz};
+    int src[3];
+    int flip[3] = {0, 0, 0};
+    bool ghost = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int s = idx[d];
+        if (s < 0) {
+            ghost = true;
+            if (g.bc[2 * d] == 0) s += n[d];
+            else { s = -1 - s; flip[d] = 1; }
+        } else if (s >= n[d]) {
+            ghost = true;
+            if (g.bc[2 * d + 1] == 0) s -= n[d];
+            else { s = 2 * n[d] - 1 - s; flip[d] = 1; }
+        }
+        src[d] = s;
+    }
+    if (!ghost) return;
+    const long long from = pidx(g, src[0], src[1], src[2]);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        double val = Q[v * g.pstride + from];
+        if (v >= 1 && v <= 3 && flip[v - 1]) val = -val;
+        Q[v * g.pstride + t] = val;
+    }
+}
+
+// dQ of the 18 big-stencil neighbours of cell (i,j,k), formed in FP64
+template <typename R>
+__device__ __forceinline__ void load_stencil(const double *__restrict__ Qv, const Geo &g, int i, int j, int k,
+                                             double qc, Stencil<R> &st)
+{
+    const long long sx = 1, sy = g.px, sz = (long long)g.px * g.py;
+    const long long c = pidx(g, i, j, k);
+    const long long sd[3] = {sx, sy, sz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        st.f[d][0] = R(Qv[c - sd[d]] - qc);
+        st.f[d][1] = R(Qv[c + sd[d]] - qc);
+    }
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const long long a = sd[p], b = sd[(p + 1) % 3];
+#pragma unroll
+        for (int sa = 0; sa < 2; ++sa)
+#pragma unroll
+            for (int sb = 0; sb < 2; ++sb) st.e[p][sa][sb] = R(Qv[c + (sa ? a : -a) + (sb ? b : -b)] - qc);
+    }
+}
+
+// literal positivity check (Sec. 4): rho and p of every P_m, m = 0..24, at
+// every one of the cell's 24 Gauss points
+template <typename R>
+__device__ __noinline__ bool positivity_violated(const double *__restrict__ Q, const Geo &g, int i, int j, int k,
+                                                 R gamma)
+{
+    R qcv[5];
+    Stencil<R> st[5];
+    for (int v = 0; v < 5; ++v) {
+        const double qc = Q[v * g.pstride + pidx(g, i, j, k)];
+        qcv[v] = R(qc);
+        load_stencil(Q + v * g.pstride, g, i, j, k, qc, st[v]);
+    }
+    for (int m = 0; m <= 24; ++m) {
+        R cf[5][9];
+        for (int v = 0; v < 5; ++v) {
+            if (m == 0) {
+                big_stencil_P0(st[v], cf[v]);
+            } else {
+                R b[3];
+                sub_stencil_rt(st[v], m - 1, b);
+                for (int n = 0; n < 9; ++n) cf[v][n] = n < 3 ? b[n] : R(0);
+            }
+        }
+        for (int gq = 0; gq < 24; ++gq) {
+            const int d = gq / 8, side = (gq / 4) & 1, ga = (gq >> 1) & 1, gb = gq & 1;
+            R X[3];
+            X[d] = side ? R(0.5) : R(-0.5);
+            X[(d + 1) % 3] = ga ? R(GAUSS_S) : R(-GAUSS_S);
+            X[(d + 2) % 3] = gb ? R(GAUSS_S) : R(-GAUSS_S);
+            R W[5];
+            for (int v = 0; v < 5; ++v) W[v] = qcv[v] + poly9(cf[v], X);
+            const R p = (gamma - R(1)) * (W[4] - R(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / W[0]);
+            if (W[0] < R(0) || p < R(0)) return true;
+        }
+    }
+    return false;
+}
+
+// WENO-AO reconstruction (Sec. 2) of one cell of the (n+2)^3 box, t its
+// linear index there; writes Q_c and the 9 coefficients of P~ - Q_c per
+// variable, and the positivity flag
+template <typename R>
+__device__ __forceinline__ void recon_item(const double *__restrict__ Q, R *__restrict__ coef,
+                                           unsigned char *__restrict__ flag, const Geo &g, const Scheme &S, Ctl *ctl,
+                                           long long t)
+{
+    if (t >= g.cstride) return;
+    const int i = (int)(t % g.cx) - 1, j = (int)((t / g.cx) % g.cy) - 1, k = (int)(t / ((long long)g.cx * g.cy)) - 1;
+    R rad[5], qcv[5];
+#pragma unroll 1
+    for (int v = 0; v < 5; ++v) {
+        const double *Qv = Q + v * g.pstride;
+        const double qc = Qv[pidx(g, i, j, k)];
+        qcv[v] = R(qc);
+        Stencil<R> st;
+        load_stencil(Qv, g, i, j, k, qc, st);
+        R out[9];
+        weno_ao(st, S, out, rad[v]);
+        coef[coef_slot(v, 0) * g.cstride + t] = R(qc);
+#pragma unroll
+        for (int n = 0; n < 9; ++n) coef[coef_slot(v, 1 + n) * g.cstride + t] = out[n];
+    }
+    // positivity fallback: the cheap sufficient test first, the literal
+    // check of all 25 polynomials at the 24 Gauss points only when it fails
+    bool bad = false;
+    if (S.limiter && !positivity_certain(qcv, rad, R(S.gamma))) bad = positivity_violated<R>(Q, g, i, j, k, R(S.gamma));
+    if (bad) {
+        for (int v = 0; v < 5; ++v)
+            for (int n = 1; n < 10; ++n) coef[coef_slot(v, n) * g.cstride + t] = R(0);
+        atomicAdd(&ctl->flagged, 1);
+    }
+    flag[t] = bad ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// Face flux: one Gauss point per call, 4 consecutive lanes per face (all 4
+// must call together: the Gauss sum uses warp shuffles).  The local frame of
+// a face normal to axis D is (e_D, e_{D+1}, e_{D+2}) (the printed frame for
+// D = x, and its cyclic images).  The stored value is the face-averaged flux
+// per unit area, F and dF/dt, in FP64.  t: 4 * face + Gauss point; t beyond
+// the faces computes a clamped face and writes nothing.
+// ---------------------------------------------------------------------------
+template <typename R, int D>
+__device__ __forceinline__ void eval_side(const R *__restrict__ coef, const Geo &g, long long ci, R xd, R xa, R xb,
+                                          R W[5], R dW[3][5])
+{
+    R X[3];
+    X[D] = xd;
+    X[(D + 1) % 3] = xa;
+    X[(D + 2) % 3] = xb;
+    const R ih = R(g.inv_h);
+    R val[5], grad[5][3];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        R c[9];
+#pragma unroll
+        for (int n = 0; n < 9; ++n) c[n] = coef[coef_slot(v, 1 + n) * g.cstride + ci];
+        R s;
+        poly_value_grad(c, X, ih, s, grad[v]);
+        val[v] = coef[coef_slot(v, 0) * g.cstride + ci] + s;
+    }
+    // local frame: local axis l is global axis (D + l) % 3
+    W[0] = val[0];
+    W[4] = val[4];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) W[1 + l] = val[1 + (D + l) % 3];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        const int gd = (D + l) % 3;
+        dW[l][0] = grad[0][gd];
+        dW[l][4] = grad[4][gd];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) dW[l][1 + m] = grad[1 + (D + m) % 3][gd];
+    }
+}
+
+template <int D> __device__ __forceinline__ long long face_count(const Geo &g)
+{
+    return (long long)(g.nx + (D == 0)) * (g.ny + (D == 1)) * (g.nz + (D == 2));
+}
+
+template <typename R, int D>
+__device__ __forceinline__ void flux_item(const R *__restrict__ coef, double *__restrict__ Fout, const Geo &g,
+                                          const Scheme &S, double dt, long long t, long long tlimit = LLONG_MAX)
+{
+    const int ex = g.nx + (D == 0), ey = g.ny + (D == 1);
+    const long long nface = face_count<D>(g);
+    long long face = t >> 2;
+    const int gp = (int)(t & 3);
+    const bool valid = face < nface && t < tlimit;
+    if (!valid) face = nface - 1;
+    // (i, j, k) is the right cell; the left cell is one step back along D
+    const int i = (int)(face % ex), j = (int)((face / ex) % ey), k = (int)(face / ((long long)ex * ey));
+    const int il = i - (D == 0), jl = j - (D == 1), kl = k - (D == 2);
+    const R xa = (gp & 2) ? R(GAUSS_S) : R(-GAUSS_S);
+    const R xb = (gp & 1) ? R(GAUSS_S) : R(-GAUSS_S);
+    R Wl[5], dWl[3][5], Wr[5], dWr[3][5];
+    eval_side<R, D>(coef, g, cidx(g, il, jl, kl), R(0.5), xa, xb, Wl, dWl);
+    eval_side<R, D>(coef, g, cidx(g, i, j, k), R(-0.5), xa, xb, Wr, dWr);
+    R F[5], dF[5];
+    gks_flux<R>(Wl, dWl, Wr, dWr, S, R(dt), F, dF);
+    // back to the global frame, Gauss weight 1/4, sum of the 4 lanes in the
+    // working precision; the face value is stored in FP64
+    R f[10];
+    f[0] = R(0.25) * F[0];
+    f[4] = R(0.25) * F[4];
+    f[5] = R(0.25) * dF[0];
+    f[9] = R(0.25) * dF[4];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        f[1 + (D + l) % 3] = R(0.25) * F[1 + l];
+        f[6 + (D + l) % 3] = R(0.25) * dF[1 + l];
+    }
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+        f[q] += __shfl_xor_sync(0xffffffffu, f[q], 1);
+        f[q] += __shfl_xor_sync(0xffffffffu, f[q], 2);
+    }
+    if (valid && gp == 0) {
+#pragma unroll
+        for (int q = 0; q < 10; ++q) Fout[q * nface + face] = double(f[q]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// update: L = -(1/h) sum over the 3 axes of (F_upper - F_lower) with the
+// face-averaged fluxes, and the two-stage fourth-order combination (Sec. 3)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cell_residual(const double *__restrict__ Fx, const double *__restrict__ Fy,
+                                              const double *__restrict__ Fz, const Geo &g, int i, int j, int k,
+                                              double L[5], double dL[5])
+{
+    const long long nfx = (long long)(g.nx + 1) * g.ny * g.nz;
+    const long long nfy = (long long)g.nx * (g.ny + 1) * g.nz;
+    const long long nfz = (long long)g.nx * g.ny * (g.nz + 1);
+    const long long fx0 = ((long long)k * g.ny + j) * (g.nx + 1) + i;
+    const long long fy0 = ((long long)k * (g.ny + 1) + j) * g.nx + i;
+    const long long fz0 = ((long long)k * g.ny + j) * g.nx + i;
+    const long long fzs = (long long)g.nx * g.ny;
+#pragma unroll
+    for (int v = 0; v < 10; ++v) {
+        const double sx = Fx[v * nfx + fx0 + 1] - Fx[v * nfx + fx0];
+        const double sy = Fy[v * nfy + fy0 + g.nx] - Fy[v * nfy + fy0];
+        const double sz = Fz[v * nfz + fz0 + fzs] - Fz[v * nfz + fz0];
+        const double r = -(sx + sy + sz) * g.inv_h;
+        if (v < 5) L[v] = r;
+        else dL[v - 5] = r;
+    }
+}
+
+// one interior cell (t < ncell) of the stage update; the call for t = 0 of
+// stage 2 also advances the instance's time and step count
+template <int STAGE>
+__device__ __forceinline__ void update_item(double *__restrict__ Qn, double *__restrict__ Qs,
+                                            double *__restrict__ Wacc, const double *__restrict__ Fx,
+                                            const double *__restrict__ Fy, const double *__restrict__ Fz,
+                                            const Geo &g, double gamma, Ctl *ctl, double dt, long long t)
+{
+    if (STAGE == 2 && t == 0) {
+        ctl->t += dt;
+        ctl->steps_done += 1;
+    }
+    if (t >= g.ncell) return;
+    const int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / ((long long)g.nx * g.ny));
+    double L[5], dL[5];
+    cell_residual(Fx, Fy, Fz, g, i, j, k, L, dL);
+    const long long pi = pidx(g, i, j, k);
+    if (STAGE == 1) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            const double q = Qn[v * g.pstride + pi];
+            Qs[v * g.pstride + pi] = q + 0.5 * dt * L[v] + 0.125 * dt * dt * dL[v];
+            Wacc[v * g.ncell + t] = q + dt * L[v] + (dt * dt / 6.0) * dL[v];
+        }
+    } else {
+        double W[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            W[v] = Wacc[v * g.ncell + t] + (dt * dt / 3.0) * dL[v];
+            Qn[v * g.pstride + pi] = W[v];
+        }
+        const double p = (gamma - 1.0) * (W[4] - 0.5 * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / W[0]);
+        if (!(W[0] > 0.0) || !(p > 0.0)) atomicOr(&ctl->status, 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CFL: dt = cfl * min_cells h/(|U| + c).  cfl_value gives one cell's
+// h/(|U| + c) (+inf beyond the cells, 0 for a nonphysical cell);
+// block_min_to reduces over the block with warp shuffles and folds into the
+// accumulator with an integer atomicMin on the bit pattern (positive
+// doubles order like their bits): order-independent, so exact.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double cfl_value(const double *__restrict__ Q, const Geo &g, double gamma, long long t)
+{
+    if (t >= g.ncell) return INFINITY;
+    const int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / ((long long)g.nx * g.ny));
+    const long long pi = pidx(g, i, j, k);
+    double W[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) W[q] = Q[q * g.pstride + pi];
+    const double rho = W[0];
+    const double m2 = W[1] * W[1] + W[2] * W[2] + W[3] * W[3];
+    const double speed = sqrt(m2) / rho;
+    const double p = (gamma - 1.0) * (W[4] - 0.5 * m2 / rho);
+    const double c = sqrt(gamma * p / rho);
+    double v = g.h / (speed + c);
+    if (!(v > 0.0)) v = 0.0;  // nonphysical: force dt = 0
+    return v;
+}
+
+// all threads of the block call it (blockDim a multiple of 32, <= 1024)
+__device__ __forceinline__ void block_min_to(double v, unsigned long long *acc)
+{
+    __shared__ double red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0) atomicMin(acc, (unsigned long long)__double_as_longlong(v));
+    }
+}
+
+// choose dt for this step and arm (or disarm) the stage kernels
+__device__ __forceinline__ void dt_choose(Ctl *ctl, double cfl, double dt_fixed, double t_end)
+{
+    double dt;
+    if (dt_fixed > 0.0) {
+        dt = dt_fixed;
+    } else {
+        dt = cfl * __longlong_as_double((long long)ctl->minbits);
+        if (ctl->t + dt > t_end) dt = t_end - ctl->t;
+    }
+    ctl->dt = dt;
+    ctl->active = (dt > 0.0) ? 1 : 0;
+    ctl->minbits = (unsigned long long)__double_as_longlong(INFINITY);
+    ctl->flagged = 0;
+}
+
+}  // namespace hk

@@ -16,6 +16,7 @@ void launch_residual(const double *Fx, const double *Fy, const double *Fz, const
                      cudaStream_t s);
 void launch_cfl(const double *Q, const Geo &g, double gamma, Ctl *ctl, cudaStream_t s);
 void launch_dt(Ctl *ctl, double cfl, double dt_fixed, double t_end, cudaStream_t s);
+void launch_init_ctl(Ctl *ctl, double t, cudaStream_t s);
 void launch_set_ctl(Ctl *ctl, double t, double dt, int active, cudaStream_t s);
 void launch_scatter(const double *src, double *Q, const Geo &g, cudaStream_t s);
 void launch_gather(const double *Q, double *dst, const Geo &g, cudaStream_t s);

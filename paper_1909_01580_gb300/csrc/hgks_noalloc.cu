@@ -171,6 +171,7 @@ extern "C" int hgks_flux_noalloc(const hgks_grid_t *grid, double gamma, double m
     // the scatter, every ghost cell by the halo, every coefficient and flag
     // of the reconstruction box by the reconstruction, every face flux by
     // the flux kernels.  Nothing of an earlier call is read.
+    hk::launch_init_ctl(ctl, 0.0, s);
     hk::launch_set_ctl(ctl, 0.0, dt, 1, s);
     hk::launch_scatter(q, Q, g, s);
     hk::launch_halo(Q, g, s);

@@ -29,7 +29,11 @@ HGKS_E_STATE = -6
 # every symbol include/hgks.h declares
 EXPORTS = ("hgks_create", "hgks_set_option", "hgks_set_state", "hgks_get_state", "hgks_step", "hgks_flux",
            "hgks_reconstruct", "hgks_point_flux", "hgks_set_timing", "hgks_get_timing", "hgks_launch_count",
-           "hgks_device_bytes", "hgks_last_error", "hgks_destroy", "hgks_flux_noalloc")
+           "hgks_device_bytes", "hgks_last_error", "hgks_destroy", "hgks_flux_noalloc",
+           "hgks_batch_create", "hgks_batch_footprint", "hgks_batch_add", "hgks_batch_remove", "hgks_batch_step",
+           "hgks_batch_poll", "hgks_batch_get_state", "hgks_batch_tune", "hgks_batch_set_tuning",
+           "hgks_batch_get_tuning", "hgks_batch_launch_count", "hgks_batch_last_error", "hgks_batch_destroy")
+HGKS_TUNE_NPARAM = 11
 
 
 class HgksError(RuntimeError):
@@ -84,6 +88,28 @@ def load(build_if_missing: bool = True):
     L.hgks_flux_noalloc.argtypes = [P(hgks_grid_t), ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                     P(ctypes.c_int), vp, ctypes.c_double, vp, vp, vp]
     L.hgks_flux_noalloc.restype = ctypes.c_int
+    ip = P(ctypes.c_int)
+    L.hgks_batch_create.argtypes = [ctypes.c_int, ctypes.c_ulonglong, ctypes.c_int, vp, P(vp)]
+    L.hgks_batch_footprint.argtypes = [P(hgks_grid_t)]
+    L.hgks_batch_footprint.restype = ctypes.c_ulonglong
+    L.hgks_batch_add.argtypes = [vp, P(hgks_grid_t), ctypes.c_double, ctypes.c_double, ctypes.c_double, ip, vp,
+                                 ctypes.c_double, ctypes.c_double, ctypes.c_double, ip]
+    L.hgks_batch_remove.argtypes = [vp, ctypes.c_int]
+    L.hgks_batch_step.argtypes = [vp, ctypes.c_int]
+    L.hgks_batch_poll.argtypes = [vp, vp, vp, vp]
+    L.hgks_batch_get_state.argtypes = [vp, ctypes.c_int, vp]
+    L.hgks_batch_tune.argtypes = [vp, ctypes.c_int, ip]
+    L.hgks_batch_set_tuning.argtypes = [vp, ip]
+    L.hgks_batch_get_tuning.argtypes = [vp, ip]
+    for name in ("hgks_batch_create", "hgks_batch_add", "hgks_batch_remove", "hgks_batch_step", "hgks_batch_poll",
+                 "hgks_batch_get_state", "hgks_batch_tune", "hgks_batch_set_tuning", "hgks_batch_get_tuning"):
+        getattr(L, name).restype = ctypes.c_int
+    L.hgks_batch_launch_count.argtypes = [vp]
+    L.hgks_batch_launch_count.restype = ctypes.c_ulonglong
+    L.hgks_batch_last_error.argtypes = [vp]
+    L.hgks_batch_last_error.restype = ctypes.c_char_p
+    L.hgks_batch_destroy.argtypes = [vp]
+    L.hgks_batch_destroy.restype = None
     L.hgks_set_timing.argtypes = [vp, ctypes.c_int]
     L.hgks_set_timing.restype = ctypes.c_int
     L.hgks_get_timing.argtypes = [vp, dp, P(ctypes.c_ulonglong)]
@@ -290,6 +316,100 @@ class Solver:
         if self.h:
             hgks_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- batched execution ----------------------------------------------------------------------
+
+def _grid(n, lo, hi, precision):
+    g = hgks_grid_t()
+    for d in range(3):
+        g.n[d], g.lo[d], g.hi[d] = int(n[d]), float(lo[d]), float(hi[d])
+    g.mesh, g.mesh_amp, g.mesh_omega, g.precision = 0, 0.0, 0.0, int(precision)
+    return g
+
+
+def _bcheck(rc, b=None):
+    if rc != HGKS_OK:
+        msg = load().hgks_batch_last_error(b)
+        raise HgksError(rc, msg.decode() if msg else "")
+
+
+def hgks_batch_footprint(n, lo, hi, precision=HGKS_FP64) -> int:
+    return int(load().hgks_batch_footprint(ctypes.byref(_grid(n, lo, hi, precision))))
+
+
+class Batch:
+    """Owner of one hgks_batch_t (marshalling only)."""
+
+    def __init__(self, precision=HGKS_FP64, arena_bytes=4 << 30, max_instances=64, stream=None):
+        self.precision = int(precision)
+        self.max_instances = int(max_instances)
+        out = ctypes.c_void_p()
+        st = None if stream is None else ctypes.c_void_p(int(stream))
+        _bcheck(load().hgks_batch_create(self.precision, int(arena_bytes), self.max_instances, st, ctypes.byref(out)))
+        self.b = out.value
+        self.n = {}
+
+    def add(self, n, lo, hi, q, t0=0.0, t_end=1.0, cfl=0.35, gamma=1.4, mu=0.0, Pr=1.0, bc=(0,) * 6):
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        g = _grid(n, lo, hi, self.precision)
+        bcs = (ctypes.c_int * 6)(*[int(x) for x in bc])
+        slot = ctypes.c_int(-1)
+        _bcheck(load().hgks_batch_add(self.b, ctypes.byref(g), float(gamma), float(mu), float(Pr), bcs, q.ctypes.data,
+                                      float(t0), float(t_end), float(cfl), ctypes.byref(slot)), self.b)
+        self.n[slot.value] = tuple(int(x) for x in n)
+        return slot.value
+
+    def remove(self, slot):
+        _bcheck(load().hgks_batch_remove(self.b, int(slot)), self.b)
+        self.n.pop(slot, None)
+
+    def step(self, nsteps=1):
+        _bcheck(load().hgks_batch_step(self.b, int(nsteps)), self.b)
+
+    def poll(self):
+        """(t, steps, state) arrays over all slots; state 0 free, 1 running,
+        2 at its end time, 3 nonphysical."""
+        t = np.zeros(self.max_instances)
+        steps = np.zeros(self.max_instances, dtype=np.int32)
+        state = np.zeros(self.max_instances, dtype=np.int32)
+        _bcheck(load().hgks_batch_poll(self.b, t.ctypes.data, steps.ctypes.data, state.ctypes.data), self.b)
+        return t, steps, state
+
+    def get_state(self, slot):
+        n = self.n[slot]
+        q = np.zeros((5, n[2], n[1], n[0]))
+        _bcheck(load().hgks_batch_get_state(self.b, int(slot), q.ctypes.data), self.b)
+        return q
+
+    def tune(self, steps_per_trial=2):
+        p = (ctypes.c_int * HGKS_TUNE_NPARAM)()
+        _bcheck(load().hgks_batch_tune(self.b, int(steps_per_trial), p), self.b)
+        return list(p)
+
+    def set_tuning(self, params):
+        p = (ctypes.c_int * HGKS_TUNE_NPARAM)(*[int(x) for x in params])
+        _bcheck(load().hgks_batch_set_tuning(self.b, p), self.b)
+
+    def get_tuning(self):
+        p = (ctypes.c_int * HGKS_TUNE_NPARAM)()
+        _bcheck(load().hgks_batch_get_tuning(self.b, p), self.b)
+        return list(p)
+
+    @property
+    def launches(self):
+        return int(load().hgks_batch_launch_count(self.b))
+
+    def close(self):
+        if getattr(self, "b", None):
+            load().hgks_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:
