@@ -1,0 +1,124 @@
+"""Pins of the oracle on mapped and moving meshes (Sec. 2 trilinear cells,
+Sec. 3 bilinear faces, Remark 2 moving mesh, Sec. 4 geometric conservation
+law): the cell volumes of the periodic mapped mesh tile the box, linear data
+are reproduced exactly on trilinear cells, and a uniform flow stays uniform
+to round-off on the moving mesh (Table 4)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_01580_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _vertex(n, lo, hi, amp, idx):
+    """mapped-mesh vertex of the static map (Sec. 4, Table 2 mesh)"""
+    xi = np.array([lo[d] + (hi[d] - lo[d]) * idx[d] / n[d] for d in range(3)])
+    s = np.prod([math.sin(2 * math.pi * (xi[d] - lo[d]) / (hi[d] - lo[d])) for d in range(3)])
+    return xi + amp * s
+
+
+def _centroid_333(n, lo, hi, amp, i, j, k):
+    """centroid of a trilinear cell by 3x3x3 Gauss quadrature (exact for the
+    integrands x J of a trilinear map)"""
+    g, w = np.polynomial.legendre.leggauss(3)
+    g, w = 0.5 * g, 0.5 * w
+    V = np.array([[[_vertex(n, lo, hi, amp, (i + a, j + b, k + c)) for c in (0, 1)] for b in (0, 1)] for a in (0, 1)])
+    vol = 0.0
+    m1 = np.zeros(3)
+    for pa, wa in zip(g, w):
+        for pb, wb in zip(g, w):
+            for pc, wc in zip(g, w):
+                p = (pa, pb, pc)
+                X = np.zeros(3)
+                J = np.zeros((3, 3))
+                for a in (0, 1):
+                    for b in (0, 1):
+                        for c in (0, 1):
+                            s = (2 * a - 1, 2 * b - 1, 2 * c - 1)
+                            f = [0.5 * (1 + 2 * s[e] * p[e]) for e in range(3)]
+                            psi = f[0] * f[1] * f[2]
+                            dpsi = [s[0] * f[1] * f[2], f[0] * s[1] * f[2], f[0] * f[1] * s[2]]
+                            X += V[a, b, c] * psi
+                            J += np.outer(V[a, b, c], dpsi)
+                dv = wa * wb * wc * abs(np.linalg.det(J))
+                vol += dv
+                m1 += dv * X
+    return m1 / vol, vol
+
+
+def test_mapped_volumes_tile_the_box():
+    for mesh, amp, omega, t in ((1, 0.1, 0.0, 0.0), (2, 0.05, 2 * math.pi, 0.13), (2, 0.1, math.pi, 0.37)):
+        cfg = oracle.make_cfg((6, 6, 6), mesh=mesh, amp=amp, omega=omega)
+        vol = oracle.volumes(cfg, t)
+        assert abs(vol.sum() - 8.0) < 1e-13
+        assert vol.min() > 0
+
+
+def test_linear_data_reproduced_on_trilinear_cells():
+    """Cell averages of a linear function are a + b . centroid; every
+    polynomial reproduces it, so P~ = P0 = the function in the cell frame."""
+    n, lo, hi, amp = (6, 6, 6), (0, 0, 0), (2, 2, 2), 0.1
+    cfg = oracle.make_cfg(n, lo, hi, mesh=1, amp=amp)
+    rng = np.random.default_rng(3)
+    base = (2.0, 0.3, 0.2, -0.1, 10.0)  # a physical state: positive pressure
+    coefs = [(base[v], rng.uniform(-0.1, 0.1, 3)) for v in range(5)]
+    q = np.zeros((5,) + n[::-1])
+    cents = {}
+    for k in range(n[2]):
+        for j in range(n[1]):
+            for i in range(n[0]):
+                c, vol = _centroid_333(n, lo, hi, amp, i, j, k)
+                cents[(i, j, k)] = (c, vol)
+                for v in range(5):
+                    q[v, k, j, i] = coefs[v][0] + coefs[v][1] @ c
+    coef, flag, a0 = oracle.reconstruct(cfg, q)
+    for (i, j, k) in [(2, 2, 2), (3, 2, 3), (2, 3, 3)]:
+        lin = i + 6 * (j + 6 * k)
+        h = cents[(i, j, k)][1] ** (1.0 / 3.0)
+        for v in range(5):
+            np.testing.assert_allclose(a0[lin, v, :3], h * coefs[v][1], rtol=0, atol=1e-13)
+            np.testing.assert_allclose(a0[lin, v, 3:], 0.0, atol=1e-13)
+            np.testing.assert_allclose(coef[lin, v, 1:], a0[lin, v], atol=1e-13)
+
+
+def test_free_stream_on_moving_mesh():
+    """Geometric conservation: uniform flow through the moving mesh of the
+    serving/benchmark map (amplitude 0.05, sin 2 pi t) stays uniform."""
+    n = (8, 8, 8)
+    cfg = oracle.make_cfg(n, mesh=2, amp=0.05, omega=2 * math.pi)
+    q = W.uniform_flow(n)
+    vol0 = oracle.volumes(cfg, 0.0).reshape(-1)
+    q1, t, done, vol = oracle.step(cfg, q, 0.0, 1000, cfl=0.35, t_end=0.25, vol=vol0)
+    assert done >= 8 and abs(t - 0.25) < 1e-14
+    assert np.abs(q1 - q).max() < 1e-13
+
+
+def test_free_stream_table4_map_8():
+    """Table 4's moving mesh (amplitude 0.1, sin pi t) to t = 0.5: the L1
+    error of the density is at round-off (the paper prints 1.19e-14 on 16^3)."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "table4_gcl_moving.txt"))
+    n = (8, 8, 8)
+    cfg = oracle.make_cfg(n, mesh=2, amp=0.1, omega=math.pi)
+    q = W.uniform_flow(n)
+    vol0 = oracle.volumes(cfg, 0.0).reshape(-1)
+    q1, t, done, vol = oracle.step(cfg, q, 0.0, 1000, cfl=0.35, t_end=0.5, vol=vol0)
+    l1 = float(np.abs(q1[0] - q[0]).reshape(-1) @ vol)
+    assert l1 < 10 * rows[0, 1], (l1, rows[0, 1])
+
+
+@pytest.mark.slow
+def test_free_stream_table4_map_16():
+    rows = np.loadtxt(os.path.join(GOLDEN, "table4_gcl_moving.txt"))
+    n = (16, 16, 16)
+    cfg = oracle.make_cfg(n, mesh=2, amp=0.1, omega=math.pi)
+    q = W.uniform_flow(n)
+    vol0 = oracle.volumes(cfg, 0.0).reshape(-1)
+    q1, t, done, vol = oracle.step(cfg, q, 0.0, 1000, cfl=0.35, t_end=0.5, vol=vol0)
+    l1 = float(np.abs(q1[0] - q[0]).reshape(-1) @ vol)
+    print(f"Table 4, 16^3: oracle L1 = {l1:.3e} (paper {rows[0, 1]:.3e})")
+    assert l1 < 10 * rows[0, 1]
