@@ -33,9 +33,16 @@ typedef struct {
     double lo[3];      /* physical box [lo, hi]                                     */
     double hi[3];
     int mesh;          /* 0: uniform mesh of cubic cells (Sec. 4 accuracy, TGV and
-                          Riemann tests); other values are rejected                 */
-    double mesh_amp;   /* reserved for mapped meshes; must be 0                     */
-    double mesh_omega; /* reserved for mapped meshes; must be 0                     */
+                             Riemann tests);
+                          1: static mapped mesh of trilinear hexahedra (Sec. 2,
+                             Sec. 4 non-coplanar mesh), x_d = xi_d + amp
+                             prod_e sin(2 pi (xi_e - lo_e)/L_e) on a uniform
+                             reference grid xi over [lo, hi];
+                          2: the same map times sin(omega t), moving with the
+                             grid velocity dx/dt (Remark 2).
+                          Mapped meshes are periodic in every direction.      */
+    double mesh_amp;   /* amp of the map (0 for mesh 0)                             */
+    double mesh_omega; /* omega of the moving map (0 for meshes 0 and 1)            */
     int precision;     /* HGKS_FP64 or HGKS_MIXED                                   */
 } hgks_grid_t;
 
@@ -83,7 +90,13 @@ int hgks_create(const hgks_grid_t *grid, double gamma, double mu, double Pr, con
  * Sec. 4), "limiter" (1/0: positivity fallback of Sec. 4). */
 int hgks_set_option(hgks_t *h, const char *key, double value);
 
-/* Load the state q ([5][nz][ny][nx] FP64, copied) at time t. */
+/* Load the state q ([5][nz][ny][nx] FP64, copied) at time t.  On a mapped
+ * mesh the cell volumes that the update divides by restart from the
+ * geometric volumes of the mesh at t.  On a moving mesh each step freezes
+ * the geometry at the start of each stage (t_n, then t_n + dt/2), takes the
+ * flux in the frame moving with the grid, advances |Omega| Q by the two-stage
+ * formula and the volume by the same formula from the swept-volume rate of
+ * the faces (discrete geometric conservation: a uniform flow stays uniform). */
 int hgks_set_state(hgks_t *h, const double *q, int on_device, double t);
 
 /* Copy the state out into q ([5][nz][ny][nx] FP64) and the time into *t

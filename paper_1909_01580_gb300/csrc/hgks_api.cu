@@ -10,6 +10,8 @@
 
 #include "../../include/hgks.h"
 #include "hgks_kernels.cuh"
+#include "hgks_mapped.cuh"
+#include "hgks_mapped_launch.cuh"
 
 using hk::Ctl;
 using hk::Geo;
@@ -28,6 +30,12 @@ struct hgks {
     double *F[3];                // face fluxes [10][nface_d]
     Ctl *ctl;                    // device control block
     Ctl *ctl_host;               // pinned mirror for read-back
+    // mapped and moving meshes (mesh 1, 2)
+    int mesh;
+    hk::MapGeo map;
+    double *geo;                 // [NGEO][pstride] cell geometry at the stage time
+    double *vol, *vnext;         // [ncell] volumes of the discrete conservation law
+    double *sintab;              // sine factors of the map at the vertex indices
     bool have_state;
     // optional per-phase timing with CUDA events on the handle's stream
     bool timing;
@@ -137,6 +145,10 @@ static void free_all(hgks_t *h)
     for (int d = 0; d < 3; ++d) cudaFree(h->F[d]);
     cudaFree(h->ctl);
     cudaFreeHost(h->ctl_host);
+    cudaFree(h->geo);
+    cudaFree(h->vol);
+    cudaFree(h->vnext);
+    cudaFree(h->sintab);
 }
 
 extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, double Pr, const int bc[6], void *stream,
@@ -149,12 +161,17 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
         if (grid->n[d] < 2 || !(grid->hi[d] > grid->lo[d]))
             return fail(nullptr, HGKS_E_INVALID, "each axis needs at least 2 cells and hi > lo%s");
     }
-    if (grid->mesh != 0 || grid->mesh_amp != 0.0 || grid->mesh_omega != 0.0)
-        return fail(nullptr, HGKS_E_INVALID, "only the uniform mesh (mesh = 0) is supported%s");
+    if (grid->mesh < 0 || grid->mesh > 2)
+        return fail(nullptr, HGKS_E_INVALID, "mesh must be 0 (uniform), 1 (static mapped) or 2 (moving)%s");
+    if (grid->mesh == 0 && (grid->mesh_amp != 0.0 || grid->mesh_omega != 0.0))
+        return fail(nullptr, HGKS_E_INVALID, "a uniform mesh takes mesh_amp = mesh_omega = 0%s");
+    if (grid->mesh != 0)
+        for (int i = 0; i < 6; ++i)
+            if (bc[i] != HGKS_BC_PERIODIC) return fail(nullptr, HGKS_E_INVALID, "mapped meshes are periodic%s");
     if (grid->precision != HGKS_FP64 && grid->precision != HGKS_MIXED)
         return fail(nullptr, HGKS_E_INVALID, "precision must be HGKS_FP64 or HGKS_MIXED%s");
     double hx = (grid->hi[0] - grid->lo[0]) / grid->n[0];
-    for (int d = 1; d < 3; ++d) {
+    for (int d = 1; d < 3 && grid->mesh == 0; ++d) {
         double hd = (grid->hi[d] - grid->lo[d]) / grid->n[d];
         if (fabs(hd - hx) > 1e-12 * hx) return fail(nullptr, HGKS_E_INVALID, "cells must be cubes%s");
     }
@@ -216,8 +233,12 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
         h->own_stream = true;
     }
     const size_t rsz = grid->precision == HGKS_MIXED ? sizeof(float) : sizeof(double);
+    h->mesh = grid->mesh;
+    const bool mapped = h->mesh != 0;
+    const int ncoef = mapped ? hk::NCOEF_M : hk::NCOEF;
+    const int nfv = mapped ? hk::NFACE_M : 10;
     size_t sizes[] = {5 * g.pstride * sizeof(double), 5 * g.pstride * sizeof(double), 5 * g.ncell * sizeof(double),
-                      hk::NCOEF * g.cstride * rsz, (size_t)g.cstride};
+                      ncoef * g.cstride * rsz, (size_t)g.cstride};
     void **ptrs[] = {(void **)&h->Qn, (void **)&h->Qs, (void **)&h->Wacc, &h->coef, (void **)&h->flag};
     bool ok = true;
     for (int i = 0; i < 5 && ok; ++i) {
@@ -225,9 +246,38 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
         h->bytes += sizes[i];
     }
     for (int d = 0; d < 3 && ok; ++d) {
-        size_t b = 10 * nface(g, d) * sizeof(double);
+        size_t b = nfv * nface(g, d) * sizeof(double);
         ok = cudaMalloc((void **)&h->F[d], b) == cudaSuccess;
         h->bytes += b;
+    }
+    if (mapped && ok) {
+        // the map x = xi + amp S(t) prod sin(2 pi (xi - lo)/L): sine factors
+        // at vertex indices -2..n+2 of each axis
+        const int nv[3] = {g.nx + 5, g.ny + 5, g.nz + 5};
+        std::vector<double> tab(nv[0] + nv[1] + nv[2]);
+        size_t o = 0;
+        for (int d = 0; d < 3; ++d)
+            for (int iv = -2; iv <= grid->n[d] + 2; ++iv, ++o) {
+                const double xi = grid->lo[d] + (grid->hi[d] - grid->lo[d]) * (double)iv / (double)grid->n[d];
+                tab[o] = sin(2.0 * M_PI * (xi - grid->lo[d]) / (grid->hi[d] - grid->lo[d]));
+            }
+        ok = cudaMalloc((void **)&h->sintab, tab.size() * sizeof(double)) == cudaSuccess &&
+             cudaMemcpy(h->sintab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+        ok = ok && cudaMalloc((void **)&h->geo, hk::NGEO * g.pstride * sizeof(double)) == cudaSuccess;
+        ok = ok && cudaMalloc((void **)&h->vol, g.ncell * sizeof(double)) == cudaSuccess;
+        ok = ok && cudaMalloc((void **)&h->vnext, g.ncell * sizeof(double)) == cudaSuccess;
+        h->bytes += tab.size() * sizeof(double) + (hk::NGEO * g.pstride + 2 * g.ncell) * sizeof(double);
+        for (int d = 0; d < 3; ++d) {
+            h->map.lo[d] = grid->lo[d];
+            h->map.hi[d] = grid->hi[d];
+            h->map.n[d] = grid->n[d];
+        }
+        h->map.amp = grid->mesh_amp;
+        h->map.omega = grid->mesh_omega;
+        h->map.moving = grid->mesh == 2;
+        h->map.sx = h->sintab;
+        h->map.sy = h->sintab + nv[0];
+        h->map.sz = h->sintab + nv[0] + nv[1];
     }
     ok = ok && cudaMalloc((void **)&h->ctl, sizeof(Ctl)) == cudaSuccess;
     ok = ok && cudaMallocHost((void **)&h->ctl_host, sizeof(Ctl)) == cudaSuccess;
@@ -295,6 +345,13 @@ extern "C" int hgks_set_state(hgks_t *h, const double *q, int on_device, double 
     hk::launch_init_ctl(h->ctl, t, h->stream);
     int rc = check_launch(h, 2);
     if (rc) return rc;
+    if (h->mesh != 0) {
+        // the volumes of the discrete conservation law start from the
+        // geometric volumes of the mesh at t
+        hk::launch_geom(h->geo, g, h->map, nullptr, 0, t, h->stream);
+        hk::launch_vol_from_geo(h->geo, h->vol, g, h->stream);
+        if ((rc = check_launch(h, 2))) return rc;
+    }
     if (!on_device) CUDA_OK(h, cudaStreamSynchronize(h->stream));
     h->have_state = true;
     return HGKS_OK;
@@ -322,8 +379,40 @@ extern "C" int hgks_get_state(hgks_t *h, double *q, int on_device, double *t)
 }
 
 // one evaluation of the fluxes of the state in Q (its ghosts are filled here)
-static int stage_fluxes(hgks_t *h, double *Q)
+// face fluxes of a stage on a mapped or moving mesh; the cell geometry of
+// the stage time is computed first (half: 0 for t_n, 1 for t_n + dt/2)
+static int stage_fluxes_mapped(hgks_t *h, double *Q, int half)
 {
+    const Geo &g = h->g;
+    cudaStream_t s = h->stream;
+    {
+        PhaseTimer t(h, HGKS_PHASE_HALO, 2);
+        hk::launch_geom(h->geo, g, h->map, h->ctl, half, 0.0, s);
+        hk::launch_halo(Q, g, s);
+    }
+    if (h->precision == HGKS_MIXED) {
+        float *c = (float *)h->coef;
+        {
+            PhaseTimer t(h, HGKS_PHASE_RECON, 1);
+            hk::launch_recon_mapped<float>(Q, h->geo, c, h->flag, g, h->map, h->S, h->ctl, half, s);
+        }
+        PhaseTimer t(h, HGKS_PHASE_FLUX, 3);
+        for (int d = 0; d < 3; ++d) hk::launch_flux_mapped<float>(d, c, h->F[d], g, h->map, h->S, h->ctl, half, s);
+    } else {
+        double *c = (double *)h->coef;
+        {
+            PhaseTimer t(h, HGKS_PHASE_RECON, 1);
+            hk::launch_recon_mapped<double>(Q, h->geo, c, h->flag, g, h->map, h->S, h->ctl, half, s);
+        }
+        PhaseTimer t(h, HGKS_PHASE_FLUX, 3);
+        for (int d = 0; d < 3; ++d) hk::launch_flux_mapped<double>(d, c, h->F[d], g, h->map, h->S, h->ctl, half, s);
+    }
+    return check_launch(h, 6);
+}
+
+static int stage_fluxes(hgks_t *h, double *Q, int half = 0)
+{
+    if (h->mesh != 0) return stage_fluxes_mapped(h, Q, half);
     const Geo &g = h->g;
     cudaStream_t s = h->stream;
     {
@@ -362,24 +451,39 @@ extern "C" int hgks_step(hgks_t *h, int nsteps, double cfl, double dt_fixed, dou
     for (int n = 0; n < nsteps; ++n) {
         int nl = 1;
         {
-            PhaseTimer t(h, HGKS_PHASE_CFL, dt_fixed > 0.0 ? 1 : 2);
+            PhaseTimer t(h, HGKS_PHASE_CFL, (dt_fixed > 0.0 ? 1 : 2) + (h->mesh != 0 ? 1 : 0));
             if (!(dt_fixed > 0.0)) {
-                hk::launch_cfl(h->Qn, g, h->S.gamma, h->ctl, s);
+                if (h->mesh != 0) {
+                    // h = |Omega|^(1/3) of the mesh at t_n
+                    hk::launch_geom(h->geo, g, h->map, h->ctl, 0, 0.0, s);
+                    hk::launch_cfl_mapped(h->Qn, h->geo, g, h->S.gamma, h->ctl, s);
+                    ++nl;
+                } else {
+                    hk::launch_cfl(h->Qn, g, h->S.gamma, h->ctl, s);
+                }
                 ++nl;
             }
             hk::launch_dt(h->ctl, cfl, dt_fixed, t_end, s);
         }
         if ((rc = check_launch(h, nl))) return rc;
-        if ((rc = stage_fluxes(h, h->Qn))) return rc;
+        if ((rc = stage_fluxes(h, h->Qn, 0))) return rc;
         {
             PhaseTimer t(h, HGKS_PHASE_UPDATE, 1);
-            hk::launch_update(1, h->Qn, h->Qs, h->Wacc, h->F[0], h->F[1], h->F[2], g, h->S.gamma, h->ctl, s);
+            if (h->mesh != 0)
+                hk::launch_update_mapped(1, h->Qn, h->Qs, h->Wacc, h->vol, h->vnext, h->F[0], h->F[1], h->F[2], g,
+                                         h->S.gamma, h->ctl, s);
+            else
+                hk::launch_update(1, h->Qn, h->Qs, h->Wacc, h->F[0], h->F[1], h->F[2], g, h->S.gamma, h->ctl, s);
         }
         if ((rc = check_launch(h, 1))) return rc;
-        if ((rc = stage_fluxes(h, h->Qs))) return rc;
+        if ((rc = stage_fluxes(h, h->Qs, 1))) return rc;
         {
             PhaseTimer t(h, HGKS_PHASE_UPDATE, 1);
-            hk::launch_update(2, h->Qn, h->Qs, h->Wacc, h->F[0], h->F[1], h->F[2], g, h->S.gamma, h->ctl, s);
+            if (h->mesh != 0)
+                hk::launch_update_mapped(2, h->Qn, h->Qs, h->Wacc, h->vol, h->vnext, h->F[0], h->F[1], h->F[2], g,
+                                         h->S.gamma, h->ctl, s);
+            else
+                hk::launch_update(2, h->Qn, h->Qs, h->Wacc, h->F[0], h->F[1], h->F[2], g, h->S.gamma, h->ctl, s);
         }
         if ((rc = check_launch(h, 1))) return rc;
         // with a finite end time, look every 16 steps whether it is reached
@@ -421,7 +525,8 @@ extern "C" int hgks_flux(hgks_t *h, double dt, double *L, double *dLdt, int on_d
         CUDA_OK(h, cudaMalloc((void **)&dL, 10 * g.ncell * sizeof(double)));
         dD = dL + 5 * g.ncell;
     }
-    hk::launch_residual(h->F[0], h->F[1], h->F[2], g, dL, dD, s);
+    if (h->mesh != 0) hk::launch_residual_mapped(h->F[0], h->F[1], h->F[2], h->geo, g, dL, dD, s);
+    else hk::launch_residual(h->F[0], h->F[1], h->F[2], g, dL, dD, s);
     rc = check_launch(h, 1);
     hk::launch_set_ctl(h->ctl, h->ctl_host->t, 0.0, 0, s);
     if (!rc) rc = check_launch(h, 1);
@@ -452,11 +557,14 @@ extern "C" int hgks_reconstruct(hgks_t *h, double *coef, int *flag)
     double *dc = nullptr;
     CUDA_OK(h, cudaMalloc((void **)&dc, 45 * g.ncell * sizeof(double) + g.ncell * sizeof(int)));
     int *df = (int *)(dc + 45 * g.ncell);
+    if (h->mesh != 0) hk::launch_geom(h->geo, g, h->map, h->ctl, 0, 0.0, s);
     if (h->precision == HGKS_MIXED) {
-        hk::launch_recon<float>(h->Qn, (float *)h->coef, h->flag, g, h->S, h->ctl, s);
+        if (h->mesh != 0) hk::launch_recon_mapped<float>(h->Qn, h->geo, (float *)h->coef, h->flag, g, h->map, h->S, h->ctl, 0, s);
+        else hk::launch_recon<float>(h->Qn, (float *)h->coef, h->flag, g, h->S, h->ctl, s);
         hk::launch_export_coef<float>((float *)h->coef, h->flag, g, dc, df, s);
     } else {
-        hk::launch_recon<double>(h->Qn, (double *)h->coef, h->flag, g, h->S, h->ctl, s);
+        if (h->mesh != 0) hk::launch_recon_mapped<double>(h->Qn, h->geo, (double *)h->coef, h->flag, g, h->map, h->S, h->ctl, 0, s);
+        else hk::launch_recon<double>(h->Qn, (double *)h->coef, h->flag, g, h->S, h->ctl, s);
         hk::launch_export_coef<double>((double *)h->coef, h->flag, g, dc, df, s);
     }
     hk::launch_set_ctl(h->ctl, h->ctl_host->t, 0.0, 0, s);

@@ -1,0 +1,168 @@
+// Kernels of the stage sweep on mapped and moving meshes (item bodies in
+// hgks_mapped.cuh).  The stage time is t_n (half = 0) or t_n + dt/2
+// (half = 1), read from the control block.
+#include "hgks_mapped.cuh"
+#include "hgks_mapped_launch.cuh"
+
+namespace hk {
+
+__device__ __forceinline__ double stage_time(const Ctl *ctl, int half) { return ctl->t + (half ? 0.5 * ctl->dt : 0.0); }
+
+// geometry of every cell of the padded box at the stage time (or at t_fixed
+// when ctl is null)
+__global__ void __launch_bounds__(128) k_geom(double *__restrict__ geo, Geo g, MapGeo m, const Ctl *ctl, int half,
+                                              double t_fixed)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.pstride) return;
+    const int i = (int)(t % g.px) - 2, j = (int)((t / g.px) % g.py) - 2, k = (int)(t / ((long long)g.px * g.py)) - 2;
+    const double ts = ctl ? stage_time(ctl, half) : t_fixed;
+    double rec[NGEO];
+    cell_geometry(m, i, j, k, map_factor(m, ts), rec);
+#pragma unroll
+    for (int e = 0; e < NGEO; ++e) geo[e * g.pstride + t] = rec[e];
+}
+
+__global__ void k_vol_from_geo(const double *__restrict__ geo, double *__restrict__ vol, Geo g)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.ncell) return;
+    const int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / ((long long)g.nx * g.ny));
+    vol[t] = geo[pidx(g, i, j, k)];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_recon_mapped(const double *__restrict__ Q, const double *__restrict__ geo,
+                                                      R *__restrict__ coef, unsigned char *__restrict__ flag, Geo g,
+                                                      MapGeo m, Scheme S, Ctl *ctl, int half)
+{
+    if (!ctl->active) return;
+    const double ts = stage_time(ctl, half);
+    recon_mapped_item<R>(Q, geo, coef, flag, g, m, map_factor(m, ts), S, ctl,
+                         (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+template <typename R, int D>
+__global__ void __launch_bounds__(128) k_flux_mapped(const R *__restrict__ coef, double *__restrict__ Fout, Geo g,
+                                                     MapGeo m, Scheme S, Ctl *ctl, int half)
+{
+    if (!ctl->active) return;
+    flux_mapped_item<R, D>(coef, Fout, g, m, stage_time(ctl, half), S, ctl->dt,
+                           (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(256) k_update_mapped(double *__restrict__ Qn, double *__restrict__ Qs,
+                                                       double *__restrict__ Wacc, double *__restrict__ vol,
+                                                       double *__restrict__ vnext, const double *__restrict__ Fx,
+                                                       const double *__restrict__ Fy, const double *__restrict__ Fz,
+                                                       Geo g, double gamma, Ctl *ctl)
+{
+    if (!ctl->active) return;
+    update_mapped_item<STAGE>(Qn, Qs, Wacc, vol, vnext, Fx, Fy, Fz, g, gamma, ctl, ctl->dt,
+                              (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// L = R/|Omega| and dL/dt with the geometric volumes of the stage geometry
+__global__ void k_residual_mapped(const double *__restrict__ Fx, const double *__restrict__ Fy,
+                                  const double *__restrict__ Fz, const double *__restrict__ geo, Geo g,
+                                  double *__restrict__ L, double *__restrict__ dL)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= g.ncell) return;
+    const int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / ((long long)g.nx * g.ny));
+    double Rr[5], dR[5], V;
+    cell_residual_mapped(Fx, Fy, Fz, g, i, j, k, Rr, dR, V);
+    const double vol = geo[pidx(g, i, j, k)];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        L[v * g.ncell + t] = Rr[v] / vol;
+        dL[v * g.ncell + t] = dR[v] / vol;
+    }
+}
+
+// CFL with h = |Omega|^(1/3) of the geometry at t_n
+__global__ void __launch_bounds__(256) k_cfl_mapped(const double *__restrict__ Q, const double *__restrict__ geo,
+                                                    Geo g, double gamma, Ctl *ctl)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double v = INFINITY;
+    if (t < g.ncell) {
+        const int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / ((long long)g.nx * g.ny));
+        const long long pi = pidx(g, i, j, k);
+        double W[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) W[q] = Q[q * g.pstride + pi];
+        const double rho = W[0];
+        const double m2 = W[1] * W[1] + W[2] * W[2] + W[3] * W[3];
+        const double speed = sqrt(m2) / rho;
+        const double p = (gamma - 1.0) * (W[4] - 0.5 * m2 / rho);
+        const double c = sqrt(gamma * p / rho);
+        v = cbrt(geo[pi]) / (speed + c);
+        if (!(v > 0.0)) v = 0.0;
+    }
+    block_min_to(v, &ctl->minbits);
+}
+
+static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+void launch_geom(double *geo, const Geo &g, const MapGeo &m, const Ctl *ctl, int half, double t_fixed,
+                 cudaStream_t s)
+{
+    k_geom<<<nblk(g.pstride, 128), 128, 0, s>>>(geo, g, m, ctl, half, t_fixed);
+}
+
+void launch_vol_from_geo(const double *geo, double *vol, const Geo &g, cudaStream_t s)
+{
+    k_vol_from_geo<<<nblk(g.ncell, 256), 256, 0, s>>>(geo, vol, g);
+}
+
+template <typename R>
+void launch_recon_mapped(const double *Q, const double *geo, R *coef, unsigned char *flag, const Geo &g,
+                         const MapGeo &m, const Scheme &S, Ctl *ctl, int half, cudaStream_t s)
+{
+    k_recon_mapped<R><<<nblk(g.cstride, 128), 128, 0, s>>>(Q, geo, coef, flag, g, m, S, ctl, half);
+}
+
+template <typename R>
+void launch_flux_mapped(int axis, const R *coef, double *F, const Geo &g, const MapGeo &m, const Scheme &S, Ctl *ctl,
+                        int half, cudaStream_t s)
+{
+    const long long nface = (long long)(g.nx + (axis == 0)) * (g.ny + (axis == 1)) * (g.nz + (axis == 2));
+    const unsigned nb = nblk(4 * nface, 128);
+    if (axis == 0) k_flux_mapped<R, 0><<<nb, 128, 0, s>>>(coef, F, g, m, S, ctl, half);
+    else if (axis == 1) k_flux_mapped<R, 1><<<nb, 128, 0, s>>>(coef, F, g, m, S, ctl, half);
+    else k_flux_mapped<R, 2><<<nb, 128, 0, s>>>(coef, F, g, m, S, ctl, half);
+}
+
+void launch_update_mapped(int stage, double *Qn, double *Qs, double *Wacc, double *vol, double *vnext,
+                          const double *Fx, const double *Fy, const double *Fz, const Geo &g, double gamma, Ctl *ctl,
+                          cudaStream_t s)
+{
+    if (stage == 1)
+        k_update_mapped<1><<<nblk(g.ncell, 256), 256, 0, s>>>(Qn, Qs, Wacc, vol, vnext, Fx, Fy, Fz, g, gamma, ctl);
+    else
+        k_update_mapped<2><<<nblk(g.ncell, 256), 256, 0, s>>>(Qn, Qs, Wacc, vol, vnext, Fx, Fy, Fz, g, gamma, ctl);
+}
+
+void launch_residual_mapped(const double *Fx, const double *Fy, const double *Fz, const double *geo, const Geo &g,
+                            double *L, double *dL, cudaStream_t s)
+{
+    k_residual_mapped<<<nblk(g.ncell, 256), 256, 0, s>>>(Fx, Fy, Fz, geo, g, L, dL);
+}
+
+void launch_cfl_mapped(const double *Q, const double *geo, const Geo &g, double gamma, Ctl *ctl, cudaStream_t s)
+{
+    k_cfl_mapped<<<nblk(g.ncell, 256), 256, 0, s>>>(Q, geo, g, gamma, ctl);
+}
+
+template void launch_recon_mapped<double>(const double *, const double *, double *, unsigned char *, const Geo &,
+                                          const MapGeo &, const Scheme &, Ctl *, int, cudaStream_t);
+template void launch_recon_mapped<float>(const double *, const double *, float *, unsigned char *, const Geo &,
+                                         const MapGeo &, const Scheme &, Ctl *, int, cudaStream_t);
+template void launch_flux_mapped<double>(int, const double *, double *, const Geo &, const MapGeo &, const Scheme &,
+                                         Ctl *, int, cudaStream_t);
+template void launch_flux_mapped<float>(int, const float *, double *, const Geo &, const MapGeo &, const Scheme &,
+                                        Ctl *, int, cudaStream_t);
+
+}  // namespace hk

@@ -1,0 +1,746 @@
+// Mapped and moving meshes of trilinear hexahedra (Sec. 2 trilinear cells,
+// Sec. 3 bilinear faces, Remark 2 moving mesh): per-cell geometry, the
+// WENO-AO reconstruction with per-cell least squares, and the face flux in
+// the frame moving with the grid.  Per-item bodies for hgks_mapped.cu.
+#pragma once
+#include "hgks_items.cuh"
+
+namespace hk {
+
+// The mesh map: x_d = xi_d + amp S(t) prod_e sin(2 pi (xi_e - lo_e)/L_e)
+// with S = 1 (static) or sin(omega t) (moving); xi on a uniform reference
+// grid.  sx/sy/sz hold the sine factor at vertex indices -2..n+2 (offset 2).
+struct MapGeo {
+    double lo[3], hi[3];
+    int n[3];
+    double amp, omega;
+    int moving;
+    const double *sx, *sy, *sz;
+};
+
+// per-cell geometry record (FP64, over the padded cell box): volume,
+// centroid, central second moments (xx, yy, zz, xy, xz, yz)
+constexpr int NGEO = 10;
+// reconstruction record per cell (working precision): 5 x (Q_c, 9
+// coefficients) as on the uniform mesh, then the cell frame: centroid (3),
+// h, and the cell means of the quadratic monomials in the scaled frame (6)
+constexpr int NCOEF_M = 60;
+constexpr int SLOT_FRAME = 50;
+
+HK_HD double map_factor(const MapGeo &m, double t) { return m.moving ? sin(m.omega * t) : 1.0; }
+
+HK_HD void vertex_pos(const MapGeo &m, int i, int j, int k, double S, double x[3])
+{
+    const int idx[3] = {i, j, k};
+    const double s = m.sx[i + 2] * m.sy[j + 2] * m.sz[k + 2];
+    const double disp = m.amp * S * s;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) x[d] = (m.lo[d] + (m.hi[d] - m.lo[d]) * (double)idx[d] / (double)m.n[d]) + disp;
+}
+
+// vertex velocity: amp omega cos(omega t) times the sine factor (moving mesh)
+HK_HD void vertex_vel(const MapGeo &m, int i, int j, int k, double C, double v[3])
+{
+    const double s = m.sx[i + 2] * m.sy[j + 2] * m.sz[k + 2];
+    const double vel = m.moving ? m.amp * m.omega * C * s : 0.0;
+    v[0] = v[1] = v[2] = vel;
+}
+
+// volume, centroid and central second moments of cell (i,j,k) by the 2x2x2
+// Gauss rule on its trilinear map (weights 1/8 times |det J|)
+HK_HD void cell_geometry(const MapGeo &m, int i, int j, int k, double S, double out[NGEO])
+{
+    double hv[2][2][2][3];
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int c = 0; c < 2; ++c) vertex_pos(m, i + a, j + b, k + c, S, hv[a][b][c]);
+    double X[8][3], w[8], vol = 0.0, m1[3] = {0, 0, 0};
+    int q = 0;
+    for (int ga = 0; ga < 2; ++ga)
+        for (int gb = 0; gb < 2; ++gb)
+            for (int gc = 0; gc < 2; ++gc, ++q) {
+                const double p[3] = {ga ? GAUSS_S : -GAUSS_S, gb ? GAUSS_S : -GAUSS_S, gc ? GAUSS_S : -GAUSS_S};
+                double x[3] = {0, 0, 0}, J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+                for (int a = 0; a < 2; ++a)
+                    for (int b = 0; b < 2; ++b)
+                        for (int c = 0; c < 2; ++c) {
+                            const double s[3] = {2.0 * a - 1.0, 2.0 * b - 1.0, 2.0 * c - 1.0};
+                            const double f0 = 0.5 * (1.0 + 2.0 * s[0] * p[0]);
+                            const double f1 = 0.5 * (1.0 + 2.0 * s[1] * p[1]);
+                            const double f2 = 0.5 * (1.0 + 2.0 * s[2] * p[2]);
+                            const double psi = f0 * f1 * f2;
+                            const double dpsi[3] = {s[0] * f1 * f2, f0 * s[1] * f2, f0 * f1 * s[2]};
+                            for (int d = 0; d < 3; ++d) {
+                                x[d] += hv[a][b][c][d] * psi;
+                                for (int e = 0; e < 3; ++e) J[d][e] += hv[a][b][c][d] * dpsi[e];
+                            }
+                        }
+                const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                                   J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                                   J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+                w[q] = 0.125 * fabs(det);
+                for (int d = 0; d < 3; ++d) X[q][d] = x[d];
+                vol += w[q];
+                for (int d = 0; d < 3; ++d) m1[d] += w[q] * x[d];
+            }
+    double cen[3] = {m1[0] / vol, m1[1] / vol, m1[2] / vol};
+    double M[6] = {0, 0, 0, 0, 0, 0};
+    for (int r = 0; r < 8; ++r) {
+        const double dx = X[r][0] - cen[0], dy = X[r][1] - cen[1], dz = X[r][2] - cen[2];
+        M[0] += w[r] * dx * dx;
+        M[1] += w[r] * dy * dy;
+        M[2] += w[r] * dz * dz;
+        M[3] += w[r] * dx * dy;
+        M[4] += w[r] * dx * dz;
+        M[5] += w[r] * dy * dz;
+    }
+    out[0] = vol;
+    for (int d = 0; d < 3; ++d) out[1 + d] = cen[d];
+    for (int e = 0; e < 6; ++e) out[4 + e] = M[e] / vol;
+}
+
+// ---------------------------------------------------------------------------
+// reconstruction on a trilinear cell: the rows of the least squares are the
+// neighbour means of the monomials in the centre cell's scaled frame minus
+// the centre cell's own; with centroid c and central second moments M of
+// each cell (per unit volume) they are, for Delta = c_nb - c_c:
+//   linear    Delta_d / h
+//   quadratic (M_nb,de - M_c,de)/h^2 + Delta_d Delta_e / h^2.
+// ---------------------------------------------------------------------------
+template <typename R> struct CellFrame {
+    double c[3];
+    double h;
+    double Mh[6];   // M_c / h^2: the cell means of the quadratic monomials
+};
+
+__device__ __forceinline__ void read_geo(const double *__restrict__ geo, const Geo &g, int i, int j, int k,
+                                         double rec[NGEO])
+{
+    const long long p = pidx(g, i, j, k);
+#pragma unroll
+    for (int e = 0; e < NGEO; ++e) rec[e] = geo[e * g.pstride + p];
+}
+
+// row of the big-stencil system for the neighbour at offset o
+template <typename R>
+__device__ __forceinline__ void neighbour_row(const double *__restrict__ geo, const Geo &g, const CellFrame<R> &F,
+                                              int i, int j, int k, R row[9])
+{
+    double rec[NGEO];
+    read_geo(geo, g, i, j, k, rec);
+    const double ih = 1.0 / F.h, ih2 = ih * ih;
+    const double D[3] = {rec[1] - F.c[0], rec[2] - F.c[1], rec[3] - F.c[2]};
+    row[0] = R(D[0] * ih);
+    row[1] = R(D[1] * ih);
+    row[2] = R(D[2] * ih);
+    row[3] = R(rec[4] * ih2 - F.Mh[0] + D[0] * D[0] * ih2);
+    row[4] = R(rec[5] * ih2 - F.Mh[1] + D[1] * D[1] * ih2);
+    row[5] = R(rec[6] * ih2 - F.Mh[2] + D[2] * D[2] * ih2);
+    row[6] = R(rec[7] * ih2 - F.Mh[3] + D[0] * D[1] * ih2);
+    row[7] = R(rec[8] * ih2 - F.Mh[4] + D[0] * D[2] * ih2);
+    row[8] = R(rec[9] * ih2 - F.Mh[5] + D[1] * D[2] * ih2);
+}
+
+// the 18 offsets of the big stencil (3x3x3 block minus centre and corners)
+__device__ __forceinline__ void big_offset(int s, int o[3])
+{
+    // enumerate k0, j0, i0 in -1..1, skipping the centre and the 8 corners
+    int cnt = 0;
+    for (int k0 = -1; k0 <= 1; ++k0)
+        for (int j0 = -1; j0 <= 1; ++j0)
+            for (int i0 = -1; i0 <= 1; ++i0) {
+                if ((i0 == 0 && j0 == 0 && k0 == 0) || (i0 * j0 * k0 != 0)) continue;
+                if (cnt == s) {
+                    o[0] = i0;
+                    o[1] = j0;
+                    o[2] = k0;
+                }
+                ++cnt;
+            }
+}
+
+// in-place Cholesky of a packed symmetric n x n matrix (lower, row-major
+// packed: A[i*(i+1)/2 + j], j <= i) and solve
+template <typename R, int N> __device__ __forceinline__ void chol_factor(R A[N * (N + 1) / 2])
+{
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            R s = A[i * (i + 1) / 2 + j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s -= A[i * (i + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
+            if (i == j) A[i * (i + 1) / 2 + i] = m_sqrt(s);
+            else A[i * (i + 1) / 2 + j] = s / A[j * (j + 1) / 2 + j];
+        }
+    }
+}
+template <typename R, int N> __device__ __forceinline__ void chol_solve(const R L[N * (N + 1) / 2], R b[N])
+{
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        R s = b[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) s -= L[i * (i + 1) / 2 + k] * b[k];
+        b[i] = s / L[i * (i + 1) / 2 + i];
+    }
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+        R s = b[i];
+#pragma unroll
+        for (int k = i + 1; k < N; ++k) s -= L[k * (k + 1) / 2 + i] * b[k];
+        b[i] = s / L[i * (i + 1) / 2 + i];
+    }
+}
+
+// offsets of the 4 cells of sub-stencil M (same family as on the uniform mesh)
+template <int M> __device__ __forceinline__ void sub_offsets(int o[4][3])
+{
+    constexpr int p = M >> 3, s = M & 7;
+    constexpr int sa = (s & 1) ? -1 : 1, sb = (s & 2) ? -1 : 1, sc = (s & 4) ? -1 : 1;
+    constexpr int a = p, b = (p + 1) % 3, c = (p + 2) % 3;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) o[r][0] = o[r][1] = o[r][2] = 0;
+    o[0][a] = sa;
+    o[1][b] = sb;
+    o[2][a] = sa;
+    o[2][b] = sb;
+    o[3][c] = sc;
+}
+
+// linear least squares over the 4 cells of a sub-stencil (3x3 normal
+// equations): rows r (linear means in the centre frame), data dq
+template <typename R> __device__ __forceinline__ void sub_lsq(const R r[4][3], const R dq[4], R bvec[3])
+{
+    R G[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    R rhs[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        G[0] += r[q][0] * r[q][0];
+        G[1] += r[q][1] * r[q][0];
+        G[2] += r[q][1] * r[q][1];
+        G[3] += r[q][2] * r[q][0];
+        G[4] += r[q][2] * r[q][1];
+        G[5] += r[q][2] * r[q][2];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) rhs[d] += r[q][d] * dq[q];
+    }
+    chol_factor<R, 3>(G);
+    chol_solve<R, 3>(G, rhs);
+    bvec[0] = rhs[0];
+    bvec[1] = rhs[1];
+    bvec[2] = rhs[2];
+}
+
+// smoothness indicator of P0 on a general cell: cell means of the squared
+// derivatives in the scaled frame, with the cell's second moments Mh
+template <typename R> __device__ __forceinline__ R beta_quadratic_mapped(const R a[9], const R Mh[6])
+{
+    // grad P0 = g_d(0) + v_d . X with v_x = (2axx, axy, axz), v_y = (axy, 2ayy, ayz), v_z = (axz, ayz, 2azz)
+    const R v[3][3] = {{R(2) * a[3], a[6], a[7]}, {a[6], R(2) * a[4], a[8]}, {a[7], a[8], R(2) * a[5]}};
+    R s = R(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const R *u = v[d];
+        const R quad = u[0] * u[0] * Mh[0] + u[1] * u[1] * Mh[1] + u[2] * u[2] * Mh[2] +
+                       R(2) * (u[0] * u[1] * Mh[3] + u[0] * u[2] * Mh[4] + u[1] * u[2] * Mh[5]);
+        s += a[d] * a[d] + quad;
+    }
+    const R d2 = R(4) * (a[3] * a[3] + a[4] * a[4] + a[5] * a[5]);
+    const R m2 = a[6] * a[6] + a[7] * a[7] + a[8] * a[8];
+    return s + d2 + m2;
+}
+
+template <typename R>
+__device__ __forceinline__ R poly9_mapped(const R c[9], const R X[3], const R Mh[6])
+{
+    return c[0] * X[0] + c[1] * X[1] + c[2] * X[2] + c[3] * (X[0] * X[0] - Mh[0]) + c[4] * (X[1] * X[1] - Mh[1]) +
+           c[5] * (X[2] * X[2] - Mh[2]) + c[6] * (X[0] * X[1] - Mh[3]) + c[7] * (X[0] * X[2] - Mh[4]) +
+           c[8] * (X[1] * X[2] - Mh[5]);
+}
+
+// the 24 face Gauss points of cell (i,j,k) in its scaled frame
+__device__ __forceinline__ void cell_gauss_point(const MapGeo &m, int i, int j, int k, double S, int gq,
+                                                 const double c[3], double h, double X[3])
+{
+    const int d = gq / 8, side = (gq / 4) & 1, ga = (gq >> 1) & 1, gb = gq & 1;
+    double p[3];
+    p[d] = side ? 0.5 : -0.5;
+    p[(d + 1) % 3] = ga ? GAUSS_S : -GAUSS_S;
+    p[(d + 2) % 3] = gb ? GAUSS_S : -GAUSS_S;
+    double x[3] = {0, 0, 0};
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int cc = 0; cc < 2; ++cc) {
+                double v[3];
+                vertex_pos(m, i + a, j + b, k + cc, S, v);
+                const double psi = 0.125 * (1.0 + 2.0 * (2 * a - 1) * p[0]) * (1.0 + 2.0 * (2 * b - 1) * p[1]) *
+                                   (1.0 + 2.0 * (2 * cc - 1) * p[2]);
+                for (int e = 0; e < 3; ++e) x[e] += v[e] * psi;
+            }
+    for (int e = 0; e < 3; ++e) X[e] = (x[e] - c[e]) / h;
+}
+
+// P0 of one variable on a trilinear cell: right-hand side A^T dQ over the
+// 18 neighbours, solved with the Cholesky factor N of the normal matrix
+template <typename R>
+__device__ __forceinline__ void p0_mapped(const double *__restrict__ Qv, const double *__restrict__ geo, const Geo &g,
+                                          const CellFrame<R> &F, const R N[45], int i, int j, int k, double qc,
+                                          R a[9])
+{
+#pragma unroll
+    for (int n = 0; n < 9; ++n) a[n] = R(0);
+#pragma unroll 1
+    for (int s = 0; s < 18; ++s) {
+        int o[3];
+        big_offset(s, o);
+        R row[9];
+        neighbour_row<R>(geo, g, F, i + o[0], j + o[1], k + o[2], row);
+        const R dq = R(Qv[pidx(g, i + o[0], j + o[1], k + o[2])] - qc);
+#pragma unroll
+        for (int n = 0; n < 9; ++n) a[n] += row[n] * dq;
+    }
+    chol_solve<R, 9>(N, a);
+}
+
+template <typename R>
+__device__ __forceinline__ void normal_matrix_mapped(const double *__restrict__ geo, const Geo &g,
+                                                     const CellFrame<R> &F, int i, int j, int k, R N[45])
+{
+#pragma unroll
+    for (int e = 0; e < 45; ++e) N[e] = R(0);
+#pragma unroll 1
+    for (int s = 0; s < 18; ++s) {
+        int o[3];
+        big_offset(s, o);
+        R row[9];
+        neighbour_row<R>(geo, g, F, i + o[0], j + o[1], k + o[2], row);
+#pragma unroll
+        for (int a = 0; a < 9; ++a)
+#pragma unroll
+            for (int b = 0; b <= a; ++b) N[a * (a + 1) / 2 + b] += row[a] * row[b];
+    }
+    chol_factor<R, 9>(N);
+}
+
+// P_m of one variable on a trilinear cell (linear least squares over its 4
+// neighbours)
+template <int M, typename R>
+__device__ __forceinline__ void pm_mapped(const double *__restrict__ Qv, const double *__restrict__ geo, const Geo &g,
+                                          const CellFrame<R> &F, int i, int j, int k, double qc, R b[3])
+{
+    int o[4][3];
+    sub_offsets<M>(o);
+    R rows[4][3], dqs[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        R row[9];
+        neighbour_row<R>(geo, g, F, i + o[r][0], j + o[r][1], k + o[r][2], row);
+        rows[r][0] = row[0];
+        rows[r][1] = row[1];
+        rows[r][2] = row[2];
+        dqs[r] = R(Qv[pidx(g, i + o[r][0], j + o[r][1], k + o[r][2])] - qc);
+    }
+    sub_lsq(rows, dqs, b);
+}
+
+template <typename R>
+__device__ __forceinline__ void pm_mapped_rt(const double *__restrict__ Qv, const double *__restrict__ geo,
+                                             const Geo &g, const CellFrame<R> &F, int i, int j, int k, double qc,
+                                             int m, R b[3])
+{
+    switch (m) {
+#define HK_PMRT(M)                                        \
+    case M:                                               \
+        pm_mapped<M, R>(Qv, geo, g, F, i, j, k, qc, b);   \
+        break;
+        HK_FOR_SUBSTENCILS(HK_PMRT)
+#undef HK_PMRT
+    default:
+        b[0] = b[1] = b[2] = R(0);
+    }
+}
+
+// literal positivity check (Sec. 4) on a trilinear cell
+template <typename R>
+__device__ __noinline__ bool positivity_violated_mapped(const double *__restrict__ Q, const double *__restrict__ geo,
+                                                        const Geo &g, const MapGeo &m, double S, int i, int j, int k,
+                                                        const CellFrame<R> &F, R gamma)
+{
+    const R Mh[6] = {R(F.Mh[0]), R(F.Mh[1]), R(F.Mh[2]), R(F.Mh[3]), R(F.Mh[4]), R(F.Mh[5])};
+    R N[45];
+    normal_matrix_mapped<R>(geo, g, F, i, j, k, N);
+    for (int mm = 0; mm <= 24; ++mm) {
+        R cf[5][9], qcv[5];
+        for (int v = 0; v < 5; ++v) {
+            const double *Qv = Q + v * g.pstride;
+            const double qc = Qv[pidx(g, i, j, k)];
+            qcv[v] = R(qc);
+            if (mm == 0) {
+                p0_mapped<R>(Qv, geo, g, F, N, i, j, k, qc, cf[v]);
+            } else {
+                R b[3];
+                pm_mapped_rt<R>(Qv, geo, g, F, i, j, k, qc, mm - 1, b);
+                for (int n = 0; n < 9; ++n) cf[v][n] = n < 3 ? b[n] : R(0);
+            }
+        }
+        for (int gq = 0; gq < 24; ++gq) {
+            double Xd[3];
+            cell_gauss_point(m, i, j, k, S, gq, F.c, F.h, Xd);
+            const R X[3] = {R(Xd[0]), R(Xd[1]), R(Xd[2])};
+            R W[5];
+            for (int v = 0; v < 5; ++v) W[v] = qcv[v] + poly9_mapped(cf[v], X, Mh);
+            const R p = (gamma - R(1)) * (W[4] - R(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / W[0]);
+            if (W[0] < R(0) || p < R(0)) return true;
+        }
+    }
+    return false;
+}
+
+template <typename R>
+__device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, const double *__restrict__ geo,
+                                                  R *__restrict__ coef, unsigned char *__restrict__ flag,
+                                                  const Geo &g, const MapGeo &m, double S, const Scheme &Sch, Ctl *ctl,
+                                                  long long t)
+{
+    if (t >= g.cstride) return;
+    const int i = (int)(t % g.cx) - 1, j = (int)((t / g.cx) % g.cy) - 1, k = (int)(t / ((long long)g.cx * g.cy)) - 1;
+    CellFrame<R> F;
+    {
+        double rec[NGEO];
+        read_geo(geo, g, i, j, k, rec);
+        F.c[0] = rec[1];
+        F.c[1] = rec[2];
+        F.c[2] = rec[3];
+        F.h = cbrt(rec[0]);
+        const double ih2 = 1.0 / (F.h * F.h);
+        for (int e = 0; e < 6; ++e) F.Mh[e] = rec[4 + e] * ih2;
+    }
+    const R Mh[6] = {R(F.Mh[0]), R(F.Mh[1]), R(F.Mh[2]), R(F.Mh[3]), R(F.Mh[4]), R(F.Mh[5])};
+    // extents of X and of the monomials over the cell's 24 face Gauss points,
+    // for the positivity bound
+    R ext[9];
+#pragma unroll
+    for (int n = 0; n < 9; ++n) ext[n] = R(0);
+#pragma unroll 1
+    for (int gq = 0; gq < 24; ++gq) {
+        double Xd[3];
+        cell_gauss_point(m, i, j, k, S, gq, F.c, F.h, Xd);
+        const R X[3] = {R(Xd[0]), R(Xd[1]), R(Xd[2])};
+        const R pn[9] = {X[0], X[1], X[2], X[0] * X[0] - Mh[0], X[1] * X[1] - Mh[1], X[2] * X[2] - Mh[2],
+                         X[0] * X[1] - Mh[3], X[0] * X[2] - Mh[4], X[1] * X[2] - Mh[5]};
+#pragma unroll
+        for (int n = 0; n < 9; ++n) ext[n] = m_max(ext[n], m_abs(pn[n]));
+    }
+    const R xmax = m_max(ext[0], m_max(ext[1], ext[2]));
+    // normal matrix of the big stencil, factored once for the 5 variables
+    R N[45];
+    normal_matrix_mapped<R>(geo, g, F, i, j, k, N);
+
+    const R g0 = R(1.0 - 24.0 * Sch.Gamma_lin), gm = R(Sch.Gamma_lin), eps = R(Sch.weno_eps);
+    const R ig0 = R(1) / g0;
+    R rad[5], qcv[5];
+#pragma unroll 1
+    for (int v = 0; v < 5; ++v) {
+        const double *Qv = Q + v * g.pstride;
+        const double qc = Qv[pidx(g, i, j, k)];
+        qcv[v] = R(qc);
+        R a[9];
+        p0_mapped<R>(Qv, geo, g, F, N, i, j, k, qc, a);
+        const R beta0 = beta_quadratic_mapped(a, Mh);
+        R tau = R(0);
+        R bsum = R(0);  // largest |b_x| + |b_y| + |b_z| over the P_m
+#define HK_MP1(M)                                                 \
+    {                                                             \
+        R b[3];                                                   \
+        pm_mapped<M, R>(Qv, geo, g, F, i, j, k, qc, b);           \
+        const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];     \
+        tau += m_abs(beta0 - bm);                                 \
+        bsum = m_max(bsum, m_abs(b[0]) + m_abs(b[1]) + m_abs(b[2])); \
+    }
+        HK_FOR_SUBSTENCILS(HK_MP1)
+#undef HK_MP1
+        tau *= R(1.0 / 24.0);
+        const R x0 = tau / (beta0 + eps);
+        const R w0 = g0 * (R(1) + (Sch.weno_pow == 2 ? x0 * x0 : x0));
+        R wsum = w0;
+        R lin[3] = {R(0), R(0), R(0)};
+#define HK_MP2(M)                                                 \
+    {                                                             \
+        R b[3];                                                   \
+        pm_mapped<M, R>(Qv, geo, g, F, i, j, k, qc, b);           \
+        const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];     \
+        const R xm = tau / (bm + eps);                            \
+        const R wm = gm * (R(1) + (Sch.weno_pow == 2 ? xm * xm : xm)); \
+        wsum += wm;                                               \
+        const R cm = wm - w0 * gm * ig0;                          \
+        lin[0] += cm * b[0];                                      \
+        lin[1] += cm * b[1];                                      \
+        lin[2] += cm * b[2];                                      \
+    }
+        HK_FOR_SUBSTENCILS(HK_MP2)
+#undef HK_MP2
+        const R iw = R(1) / wsum;
+        const R f0 = w0 * ig0;
+        coef[coef_slot(v, 0) * g.cstride + t] = R(qc);
+#pragma unroll
+        for (int n = 0; n < 9; ++n)
+            coef[coef_slot(v, 1 + n) * g.cstride + t] = iw * (f0 * a[n] + (n < 3 ? lin[n] : R(0)));
+        // rigorous bound of |P_m - Q_c| at the Gauss points for all 25 P_m
+        R r0 = R(0);
+#pragma unroll
+        for (int n = 0; n < 9; ++n) r0 += m_abs(a[n]) * ext[n];
+        rad[v] = m_max(r0, bsum * xmax) * R(1.0000001);
+    }
+    bool bad = false;
+    if (Sch.limiter && !positivity_certain(qcv, rad, R(Sch.gamma)))
+        bad = positivity_violated_mapped<R>(Q, geo, g, m, S, i, j, k, F, R(Sch.gamma));
+    if (bad) {
+        for (int v = 0; v < 5; ++v)
+            for (int n = 1; n < 10; ++n) coef[coef_slot(v, n) * g.cstride + t] = R(0);
+        atomicAdd(&ctl->flagged, 1);
+    }
+    flag[t] = bad ? 1 : 0;
+    // the cell frame for the flux kernels
+    coef[(SLOT_FRAME + 0) * g.cstride + t] = R(F.c[0]);
+    coef[(SLOT_FRAME + 1) * g.cstride + t] = R(F.c[1]);
+    coef[(SLOT_FRAME + 2) * g.cstride + t] = R(F.c[2]);
+    coef[(SLOT_FRAME + 3) * g.cstride + t] = R(F.h);
+#pragma unroll
+    for (int e = 0; e < 6; ++e) coef[(SLOT_FRAME + 4 + e) * g.cstride + t] = Mh[e];
+}
+
+// ---------------------------------------------------------------------------
+// face flux on a bilinear face moving with the grid: one Gauss point per
+// call, 4 lanes per face; stores the face-integrated flux (weight 1/4 times
+// |X_a x X_b|), its time derivative and the swept volume rate
+// (1/4 |X_a x X_b| U_g . n) -- 11 FP64 values per face.
+// ---------------------------------------------------------------------------
+constexpr int NFACE_M = 11;
+
+template <typename R>
+__device__ __forceinline__ void eval_cell_mapped(const R *__restrict__ coef, const Geo &g, long long ci,
+                                                 const double xg[3], R val[5], R grad[5][3])
+{
+    R c[3], h, Mh[6];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) c[e] = coef[(SLOT_FRAME + e) * g.cstride + ci];
+    h = coef[(SLOT_FRAME + 3) * g.cstride + ci];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) Mh[e] = coef[(SLOT_FRAME + 4 + e) * g.cstride + ci];
+    const R ih = R(1) / h;
+    const R X[3] = {(R(xg[0]) - c[0]) * ih, (R(xg[1]) - c[1]) * ih, (R(xg[2]) - c[2]) * ih};
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        R a[9];
+#pragma unroll
+        for (int n = 0; n < 9; ++n) a[n] = coef[coef_slot(v, 1 + n) * g.cstride + ci];
+        val[v] = coef[coef_slot(v, 0) * g.cstride + ci] + poly9_mapped(a, X, Mh);
+        grad[v][0] = (a[0] + R(2) * a[3] * X[0] + a[6] * X[1] + a[7] * X[2]) * ih;
+        grad[v][1] = (a[1] + R(2) * a[4] * X[1] + a[6] * X[0] + a[8] * X[2]) * ih;
+        grad[v][2] = (a[2] + R(2) * a[5] * X[2] + a[7] * X[0] + a[8] * X[1]) * ih;
+    }
+}
+
+template <typename R, int D>
+__device__ __forceinline__ void flux_mapped_item(const R *__restrict__ coef, double *__restrict__ Fout, const Geo &g,
+                                                 const MapGeo &m, double t_stage, const Scheme &S, double dt,
+                                                 long long t)
+{
+    const int ex = g.nx + (D == 0), ey = g.ny + (D == 1);
+    const long long nface = face_count<D>(g);
+    long long face = t >> 2;
+    const int gp = (int)(t & 3);
+    const bool valid = face < nface;
+    if (!valid) face = nface - 1;
+    const int i = (int)(face % ex), j = (int)((face / ex) % ey), k = (int)(face / ((long long)ex * ey));
+    const int il = i - (D == 0), jl = j - (D == 1), kl = k - (D == 2);
+    constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
+    const double Sf = map_factor(m, t_stage);
+    const double Cf = m.moving ? cos(m.omega * t_stage) : 0.0;
+    const double ea = (gp & 2) ? GAUSS_S : -GAUSS_S, eb = (gp & 1) ? GAUSS_S : -GAUSS_S;
+    // bilinear face through the 4 vertices (i,j,k) + {0,1} e_A + {0,1} e_B
+    double X[3] = {0, 0, 0}, Xa[3] = {0, 0, 0}, Xb[3] = {0, 0, 0}, Vg[3] = {0, 0, 0};
+#pragma unroll
+    for (int sa = 0; sa < 2; ++sa)
+#pragma unroll
+        for (int sb = 0; sb < 2; ++sb) {
+            int o[3] = {0, 0, 0};
+            o[A] = sa;
+            o[B] = sb;
+            double v[3], u[3];
+            vertex_pos(m, i + o[0], j + o[1], k + o[2], Sf, v);
+            vertex_vel(m, i + o[0], j + o[1], k + o[2], Cf, u);
+            const double qa = 2.0 * sa - 1.0, qb = 2.0 * sb - 1.0;
+            const double phi = 0.25 * (1.0 + 2.0 * qa * ea) * (1.0 + 2.0 * qb * eb);
+            const double pa = 0.5 * qa * (1.0 + 2.0 * qb * eb);
+            const double pb = 0.5 * qb * (1.0 + 2.0 * qa * ea);
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                X[e] += v[e] * phi;
+                Xa[e] += v[e] * pa;
+                Xb[e] += v[e] * pb;
+                Vg[e] += u[e] * phi;
+            }
+        }
+    const double nrm[3] = {Xa[1] * Xb[2] - Xa[2] * Xb[1], Xa[2] * Xb[0] - Xa[0] * Xb[2], Xa[0] * Xb[1] - Xa[1] * Xb[0]};
+    const double area = sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+    const double lb = sqrt(Xb[0] * Xb[0] + Xb[1] * Xb[1] + Xb[2] * Xb[2]);
+    double fr[3][3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        fr[0][e] = nrm[e] / area;
+        fr[2][e] = Xb[e] / lb;
+    }
+    fr[1][0] = fr[2][1] * fr[0][2] - fr[2][2] * fr[0][1];
+    fr[1][1] = fr[2][2] * fr[0][0] - fr[2][0] * fr[0][2];
+    fr[1][2] = fr[2][0] * fr[0][1] - fr[2][1] * fr[0][0];
+    // both cells' values and gradients, rotated to the face frame
+    R Wc[2][5], dWc[2][3][5];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        R val[5], grad[5][3];
+        eval_cell_mapped<R>(coef, g, s ? cidx(g, i, j, k) : cidx(g, il, jl, kl), X, val, grad);
+        const R f[3][3] = {{R(fr[0][0]), R(fr[0][1]), R(fr[0][2])},
+                           {R(fr[1][0]), R(fr[1][1]), R(fr[1][2])},
+                           {R(fr[2][0]), R(fr[2][1]), R(fr[2][2])}};
+        Wc[s][0] = val[0];
+        Wc[s][4] = val[4];
+#pragma unroll
+        for (int l = 0; l < 3; ++l) Wc[s][1 + l] = val[1] * f[l][0] + val[2] * f[l][1] + val[3] * f[l][2];
+#pragma unroll
+        for (int di = 0; di < 3; ++di) {
+            R dd[5];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) dd[v] = grad[v][0] * f[di][0] + grad[v][1] * f[di][1] + grad[v][2] * f[di][2];
+            dWc[s][di][0] = dd[0];
+            dWc[s][di][4] = dd[4];
+#pragma unroll
+            for (int l = 0; l < 3; ++l) dWc[s][di][1 + l] = dd[1] * f[l][0] + dd[2] * f[l][1] + dd[3] * f[l][2];
+        }
+    }
+    // the frame moving with the grid (Remark 2): shift the states by U_g
+    R Ug[3];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) Ug[l] = R(Vg[0] * fr[l][0] + Vg[1] * fr[l][1] + Vg[2] * fr[l][2]);
+    const R u2 = Ug[0] * Ug[0] + Ug[1] * Ug[1] + Ug[2] * Ug[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        R *W = Wc[s];
+        W[4] = W[4] - (Ug[0] * W[1] + Ug[1] * W[2] + Ug[2] * W[3]) + R(0.5) * u2 * W[0];
+#pragma unroll
+        for (int l = 0; l < 3; ++l) W[1 + l] = W[1 + l] - Ug[l] * W[0];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            R *dW = dWc[s][e];
+            dW[4] = dW[4] - (Ug[0] * dW[1] + Ug[1] * dW[2] + Ug[2] * dW[3]) + R(0.5) * u2 * dW[0];
+#pragma unroll
+            for (int l = 0; l < 3; ++l) dW[1 + l] = dW[1 + l] - Ug[l] * dW[0];
+        }
+    }
+    R Fl[5], dFl[5];
+    gks_flux<R>(Wc[0], dWc[0], Wc[1], dWc[1], S, R(dt), Fl, dFl);
+    // back from the grid frame (u = u_rel + U_g), then to the global frame
+    R Fb[5], dFb[5];
+    Fb[0] = Fl[0];
+    dFb[0] = dFl[0];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        Fb[1 + l] = Fl[1 + l] + Ug[l] * Fl[0];
+        dFb[1 + l] = dFl[1 + l] + Ug[l] * dFl[0];
+    }
+    Fb[4] = Fl[4] + Ug[0] * Fl[1] + Ug[1] * Fl[2] + Ug[2] * Fl[3] + R(0.5) * u2 * Fl[0];
+    dFb[4] = dFl[4] + Ug[0] * dFl[1] + Ug[1] * dFl[2] + Ug[2] * dFl[3] + R(0.5) * u2 * dFl[0];
+    const R wgt = R(0.25 * area);
+    R f[NFACE_M];
+    f[0] = wgt * Fb[0];
+    f[4] = wgt * Fb[4];
+    f[5] = wgt * dFb[0];
+    f[9] = wgt * dFb[4];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        // the frame is orthonormal: its inverse is its transpose
+        f[1 + e] = wgt * (R(fr[0][e]) * Fb[1] + R(fr[1][e]) * Fb[2] + R(fr[2][e]) * Fb[3]);
+        f[6 + e] = wgt * (R(fr[0][e]) * dFb[1] + R(fr[1][e]) * dFb[2] + R(fr[2][e]) * dFb[3]);
+    }
+    f[10] = R(0.25 * (Vg[0] * nrm[0] + Vg[1] * nrm[1] + Vg[2] * nrm[2]));
+#pragma unroll
+    for (int q = 0; q < NFACE_M; ++q) {
+        f[q] += __shfl_xor_sync(0xffffffffu, f[q], 1);
+        f[q] += __shfl_xor_sync(0xffffffffu, f[q], 2);
+    }
+    if (valid && gp == 0) {
+#pragma unroll
+        for (int q = 0; q < NFACE_M; ++q) Fout[q * nface + face] = double(f[q]);
+    }
+}
+
+// residual R = -sum of the outward face-integrated fluxes, dR/dt, and the
+// swept volume rate V of cell (i,j,k)
+__device__ __forceinline__ void cell_residual_mapped(const double *__restrict__ Fx, const double *__restrict__ Fy,
+                                                     const double *__restrict__ Fz, const Geo &g, int i, int j, int k,
+                                                     double Rr[5], double dR[5], double &V)
+{
+    const long long nfx = (long long)(g.nx + 1) * g.ny * g.nz;
+    const long long nfy = (long long)g.nx * (g.ny + 1) * g.nz;
+    const long long nfz = (long long)g.nx * g.ny * (g.nz + 1);
+    const long long fx0 = ((long long)k * g.ny + j) * (g.nx + 1) + i;
+    const long long fy0 = ((long long)k * (g.ny + 1) + j) * g.nx + i;
+    const long long fz0 = ((long long)k * g.ny + j) * g.nx + i;
+    const long long fzs = (long long)g.nx * g.ny;
+#pragma unroll
+    for (int v = 0; v < NFACE_M; ++v) {
+        const double sx = Fx[v * nfx + fx0 + 1] - Fx[v * nfx + fx0];
+        const double sy = Fy[v * nfy + fy0 + g.nx] - Fy[v * nfy + fy0];
+        const double sz = Fz[v * nfz + fz0 + fzs] - Fz[v * nfz + fz0];
+        const double r = -(sx + sy + sz);
+        if (v < 5) Rr[v] = r;
+        else if (v < 10) dR[v - 5] = r;
+        else V = -r;
+    }
+}
+
+// two-stage update of |Omega| Q with the volume advanced by the same
+// formula from the swept rate (discrete geometric conservation law); vol is
+// that volume at t_n, vnext receives it at t_{n+1}
+template <int STAGE>
+__device__ __forceinline__ void update_mapped_item(double *__restrict__ Qn, double *__restrict__ Qs,
+                                                   double *__restrict__ Wacc, double *__restrict__ vol,
+                                                   double *__restrict__ vnext, const double *__restrict__ Fx,
+                                                   const double *__restrict__ Fy, const double *__restrict__ Fz,
+                                                   const Geo &g, double gamma, Ctl *ctl, double dt, long long t)
+{
+    if (STAGE == 2 && t == 0) {
+        ctl->t += dt;
+        ctl->steps_done += 1;
+    }
+    if (t >= g.ncell) return;
+    const int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / ((long long)g.nx * g.ny));
+    double Rr[5], dR[5], V;
+    cell_residual_mapped(Fx, Fy, Fz, g, i, j, k, Rr, dR, V);
+    const long long pi = pidx(g, i, j, k);
+    if (STAGE == 1) {
+        const double v0 = vol[t];
+        const double vs = v0 + 0.5 * dt * V;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const double x = v0 * Qn[q * g.pstride + pi];
+            Qs[q * g.pstride + pi] = (x + 0.5 * dt * Rr[q] + 0.125 * dt * dt * dR[q]) / vs;
+            Wacc[q * g.ncell + t] = x + dt * Rr[q] + (dt * dt / 6.0) * dR[q];
+        }
+        vnext[t] = v0 + dt * V;
+    } else {
+        const double vn = vnext[t];
+        double W[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            W[q] = (Wacc[q * g.ncell + t] + (dt * dt / 3.0) * dR[q]) / vn;
+            Qn[q * g.pstride + pi] = W[q];
+        }
+        vol[t] = vn;
+        const double p = (gamma - 1.0) * (W[4] - 0.5 * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / W[0]);
+        if (!(W[0] > 0.0) || !(p > 0.0)) atomicOr(&ctl->status, 1);
+    }
+}
+
+}  // namespace hk

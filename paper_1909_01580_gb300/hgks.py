@@ -151,11 +151,12 @@ def _ptr(a):
 
 # ---- functions with the C names -------------------------------------------------------------
 
-def hgks_create(n, lo, hi, gamma=1.4, mu=0.0, Pr=1.0, bc=(0, 0, 0, 0, 0, 0), precision=HGKS_FP64, stream=None):
+def hgks_create(n, lo, hi, gamma=1.4, mu=0.0, Pr=1.0, bc=(0, 0, 0, 0, 0, 0), precision=HGKS_FP64, stream=None,
+                mesh=0, mesh_amp=0.0, mesh_omega=0.0):
     g = hgks_grid_t()
     for d in range(3):
         g.n[d], g.lo[d], g.hi[d] = int(n[d]), float(lo[d]), float(hi[d])
-    g.mesh, g.mesh_amp, g.mesh_omega, g.precision = 0, 0.0, 0.0, int(precision)
+    g.mesh, g.mesh_amp, g.mesh_omega, g.precision = int(mesh), float(mesh_amp), float(mesh_omega), int(precision)
     bcs = (ctypes.c_int * 6)(*[int(b) for b in bc])
     out = ctypes.c_void_p()
     st = None if stream is None else ctypes.c_void_p(int(stream))
@@ -276,9 +277,10 @@ class Solver:
     """Convenience owner of one handle (still only marshalling)."""
 
     def __init__(self, n, lo, hi, gamma=1.4, mu=0.0, Pr=1.0, bc=(0,) * 6, precision=HGKS_FP64, stream=None,
+                 mesh=0, mesh_amp=0.0, mesh_omega=0.0,
                  **options):
         self.n = tuple(int(x) for x in n)
-        self.h = hgks_create(self.n, lo, hi, gamma, mu, Pr, bc, precision, stream)
+        self.h = hgks_create(self.n, lo, hi, gamma, mu, Pr, bc, precision, stream, mesh, mesh_amp, mesh_omega)
         for k, v in options.items():
             hgks_set_option(self.h, k, v)
 
