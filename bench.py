@@ -224,6 +224,41 @@ def run_gpu(args, rank, world, local, dist):
     return results
 
 
+def moving_run(steps, warmup, n=96):
+    """Density advection on the moving mesh x = xi + 0.05 sin(2 pi t)
+    prod_d sin(pi xi_d) over [0,2]^3 (n^3 cells, CFL 0.35): cell-stage
+    updates/s of the FP64 and mixed paths, CUDA events on the handle's
+    stream, with the per-phase split (geometry included)."""
+    import torch
+    from paper_1909_01580_gb300 import hgks, workloads
+    q0 = workloads.density_advection((n, n, n))
+    out = {"workload": f"density advection {n}^3 on the moving mesh (amplitude 0.05, omega 2 pi), CFL 0.35"}
+    for name, prec in (("fp64", hgks.HGKS_FP64), ("mixed", hgks.HGKS_MIXED)):
+        stream = torch.cuda.Stream()
+        s = hgks.Solver((n, n, n), (0, 0, 0), (2, 2, 2), precision=prec, stream=stream.cuda_stream,
+                        mesh=2, mesh_amp=0.05, mesh_omega=2 * math.pi)
+        s.set_state(q0, t=0.0)
+        s.step(warmup, cfl=0.35)
+        hgks.hgks_set_timing(s.h, 1)
+        torch.cuda.synchronize()
+        l0 = s.launches
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        s.step(steps, cfl=0.35, sync=False)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        timing = hgks.hgks_get_timing(s.h)
+        out[name] = {"value": n ** 3 * 2 * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+                     "steps": steps, "launches": s.launches - l0,
+                     "phase_ms_per_step": {k: round(v[0] / steps, 4) for k, v in timing.items()},
+                     "note": "the halo phase includes the cell-geometry kernel of each stage"}
+        s.close()
+        del stream
+    return out
+
+
 def serving_run(count=16, sizes=(24, 32, 48), steps=(20, 40), seed=0, load=1.25, precisions=("fp64", "mixed"),
                 arena_gb=4.0):
     """Serving workload: seeded requests (density advection / TGV 50:50,
@@ -318,6 +353,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the small serving run of the default line")
+    ap.add_argument("--no-moving", action="store_true", help="skip the 96^3 moving-mesh run of the default line")
     ap.add_argument("--serving", action="store_true",
                     help="only the serving benchmark: 64 requests on 24^3..96^3, printed as its own line")
     ap.add_argument("--serving-steps-max", type=int, default=80)
@@ -375,6 +411,8 @@ def main():
         if "e2e" in main_r:
             line["e2e"] = main_r["e2e"]
             line["mixed"]["e2e"] = res["mixed"].get("e2e")
+        if not args.no_moving and world == 1:
+            line["moving_mesh"] = moving_run(steps=max(1, min(args.steps, 5)), warmup=2)
         if not args.no_serving and world == 1:
             line["serving"] = serving_run()
         if not args.no_cpu_baseline and world == 1:

@@ -381,19 +381,20 @@ extern "C" int hgks_get_state(hgks_t *h, double *q, int on_device, double *t)
 // one evaluation of the fluxes of the state in Q (its ghosts are filled here)
 // face fluxes of a stage on a mapped or moving mesh; the cell geometry of
 // the stage time is computed first (half: 0 for t_n, 1 for t_n + dt/2)
-static int stage_fluxes_mapped(hgks_t *h, double *Q, int half)
+// unless geom_ready says the CFL reduction of this step already did it
+static int stage_fluxes_mapped(hgks_t *h, double *Q, int half, bool geom_ready)
 {
     const Geo &g = h->g;
     cudaStream_t s = h->stream;
     {
-        PhaseTimer t(h, HGKS_PHASE_HALO, 2);
-        hk::launch_geom(h->geo, g, h->map, h->ctl, half, 0.0, s);
+        PhaseTimer t(h, HGKS_PHASE_HALO, geom_ready ? 1 : 2);
+        if (!geom_ready) hk::launch_geom(h->geo, g, h->map, h->ctl, half, 0.0, s);
         hk::launch_halo(Q, g, s);
     }
     if (h->precision == HGKS_MIXED) {
         float *c = (float *)h->coef;
         {
-            PhaseTimer t(h, HGKS_PHASE_RECON, 1);
+            PhaseTimer t(h, HGKS_PHASE_RECON, 2);
             hk::launch_recon_mapped<float>(Q, h->geo, c, h->flag, g, h->map, h->S, h->ctl, half, s);
         }
         PhaseTimer t(h, HGKS_PHASE_FLUX, 3);
@@ -401,18 +402,19 @@ static int stage_fluxes_mapped(hgks_t *h, double *Q, int half)
     } else {
         double *c = (double *)h->coef;
         {
-            PhaseTimer t(h, HGKS_PHASE_RECON, 1);
+            PhaseTimer t(h, HGKS_PHASE_RECON, 2);
             hk::launch_recon_mapped<double>(Q, h->geo, c, h->flag, g, h->map, h->S, h->ctl, half, s);
         }
         PhaseTimer t(h, HGKS_PHASE_FLUX, 3);
         for (int d = 0; d < 3; ++d) hk::launch_flux_mapped<double>(d, c, h->F[d], g, h->map, h->S, h->ctl, half, s);
     }
-    return check_launch(h, 6);
+    // geometry, halo, reconstruction and its positivity pass, three face sweeps
+    return check_launch(h, geom_ready ? 6 : 7);
 }
 
-static int stage_fluxes(hgks_t *h, double *Q, int half = 0)
+static int stage_fluxes(hgks_t *h, double *Q, int half = 0, bool geom_ready = false)
 {
-    if (h->mesh != 0) return stage_fluxes_mapped(h, Q, half);
+    if (h->mesh != 0) return stage_fluxes_mapped(h, Q, half, geom_ready);
     const Geo &g = h->g;
     cudaStream_t s = h->stream;
     {
@@ -466,7 +468,8 @@ extern "C" int hgks_step(hgks_t *h, int nsteps, double cfl, double dt_fixed, dou
             hk::launch_dt(h->ctl, cfl, dt_fixed, t_end, s);
         }
         if ((rc = check_launch(h, nl))) return rc;
-        if ((rc = stage_fluxes(h, h->Qn, 0))) return rc;
+        // on a mapped mesh the CFL reduction computed the geometry of t_n
+        if ((rc = stage_fluxes(h, h->Qn, 0, h->mesh != 0 && !(dt_fixed > 0.0)))) return rc;
         {
             PhaseTimer t(h, HGKS_PHASE_UPDATE, 1);
             if (h->mesh != 0)
@@ -568,7 +571,9 @@ extern "C" int hgks_reconstruct(hgks_t *h, double *coef, int *flag)
         hk::launch_export_coef<double>((double *)h->coef, h->flag, g, dc, df, s);
     }
     hk::launch_set_ctl(h->ctl, h->ctl_host->t, 0.0, 0, s);
-    rc = check_launch(h, 3);
+    // reconstruction, export and control reset; on a mapped mesh also the
+    // geometry and the positivity pass
+    rc = check_launch(h, 3 + (h->mesh != 0 ? 2 : 0));
     if (!rc) {
         cudaMemcpyAsync(coef, dc, 45 * g.ncell * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (flag) cudaMemcpyAsync(flag, df, g.ncell * sizeof(int), cudaMemcpyDeviceToHost, s);

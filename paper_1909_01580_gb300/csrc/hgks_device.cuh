@@ -79,6 +79,8 @@ struct Ctl {
     int status;                  // bit 0: nonphysical state produced
     int steps_done;
     int flagged;                 // cells that took the positivity fallback (last stage)
+    double mapS, mapC;           // mapped mesh: sin(omega t), cos(omega t) at the stage time
+                                 // (S = 1, C = 0 on a static mesh), set by the geometry kernel
 };
 
 // ---------------------------------------------------------------------------

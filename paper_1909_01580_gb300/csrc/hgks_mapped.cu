@@ -10,15 +10,22 @@ __device__ __forceinline__ double stage_time(const Ctl *ctl, int half) { return 
 
 // geometry of every cell of the padded box at the stage time (or at t_fixed
 // when ctl is null)
-__global__ void __launch_bounds__(128) k_geom(double *__restrict__ geo, Geo g, MapGeo m, const Ctl *ctl, int half,
+__global__ void __launch_bounds__(128) k_geom(double *__restrict__ geo, Geo g, MapGeo m, Ctl *ctl, int half,
                                               double t_fixed)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.pstride) return;
     const int i = (int)(t % g.px) - 2, j = (int)((t / g.px) % g.py) - 2, k = (int)(t / ((long long)g.px * g.py)) - 2;
     const double ts = ctl ? stage_time(ctl, half) : t_fixed;
+    const double Sf = map_factor(m, ts);
+    if (ctl && t == 0) {
+        // the map's time factors of this stage, for the reconstruction and
+        // flux kernels that follow
+        ctl->mapS = Sf;
+        ctl->mapC = m.moving ? cos(m.omega * ts) : 0.0;
+    }
     double rec[NGEO];
-    cell_geometry(m, i, j, k, map_factor(m, ts), rec);
+    cell_geometry(m, i, j, k, Sf, rec);
 #pragma unroll
     for (int e = 0; e < NGEO; ++e) geo[e * g.pstride + t] = rec[e];
 }
@@ -32,14 +39,24 @@ __global__ void k_vol_from_geo(const double *__restrict__ geo, double *__restric
 }
 
 template <typename R>
-__global__ void __launch_bounds__(128) k_recon_mapped(const double *__restrict__ Q, const double *__restrict__ geo,
-                                                      R *__restrict__ coef, unsigned char *__restrict__ flag, Geo g,
-                                                      MapGeo m, Scheme S, Ctl *ctl, int half)
+__global__ void __launch_bounds__(RM_BS) k_recon_mapped(const double *__restrict__ Q, const double *__restrict__ geo,
+                                                        R *__restrict__ coef, unsigned char *__restrict__ flag, Geo g,
+                                                        MapGeo m, Scheme S, Ctl *ctl, int half)
+{
+    __shared__ R stage[RmStage<R>::n * RM_BS];
+    if (!ctl->active) return;
+    recon_mapped_item<R>(Q, geo, coef, flag, g, m, ctl->mapS, S, ctl, stage + threadIdx.x,
+                         (long long)blockIdx.x * RM_BS + threadIdx.x);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_positivity_mapped(const double *__restrict__ Q, const double *__restrict__ geo,
+                                                           R *__restrict__ coef, unsigned char *__restrict__ flag,
+                                                           Geo g, MapGeo m, Scheme S, Ctl *ctl, int half)
 {
     if (!ctl->active) return;
-    const double ts = stage_time(ctl, half);
-    recon_mapped_item<R>(Q, geo, coef, flag, g, m, map_factor(m, ts), S, ctl,
-                         (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    positivity_mapped_item<R>(Q, geo, coef, flag, g, m, ctl->mapS, S, ctl,
+                              (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 template <typename R, int D>
@@ -47,7 +64,7 @@ __global__ void __launch_bounds__(128) k_flux_mapped(const R *__restrict__ coef,
                                                      MapGeo m, Scheme S, Ctl *ctl, int half)
 {
     if (!ctl->active) return;
-    flux_mapped_item<R, D>(coef, Fout, g, m, stage_time(ctl, half), S, ctl->dt,
+    flux_mapped_item<R, D>(coef, Fout, g, m, ctl->mapS, ctl->mapC, S, ctl->dt,
                            (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -106,7 +123,7 @@ __global__ void __launch_bounds__(256) k_cfl_mapped(const double *__restrict__ Q
 
 static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
-void launch_geom(double *geo, const Geo &g, const MapGeo &m, const Ctl *ctl, int half, double t_fixed,
+void launch_geom(double *geo, const Geo &g, const MapGeo &m, Ctl *ctl, int half, double t_fixed,
                  cudaStream_t s)
 {
     k_geom<<<nblk(g.pstride, 128), 128, 0, s>>>(geo, g, m, ctl, half, t_fixed);
@@ -121,7 +138,8 @@ template <typename R>
 void launch_recon_mapped(const double *Q, const double *geo, R *coef, unsigned char *flag, const Geo &g,
                          const MapGeo &m, const Scheme &S, Ctl *ctl, int half, cudaStream_t s)
 {
-    k_recon_mapped<R><<<nblk(g.cstride, 128), 128, 0, s>>>(Q, geo, coef, flag, g, m, S, ctl, half);
+    k_recon_mapped<R><<<nblk(g.cstride, RM_BS), RM_BS, 0, s>>>(Q, geo, coef, flag, g, m, S, ctl, half);
+    k_positivity_mapped<R><<<nblk(g.cstride, 128), 128, 0, s>>>(Q, geo, coef, flag, g, m, S, ctl, half);
 }
 
 template <typename R>

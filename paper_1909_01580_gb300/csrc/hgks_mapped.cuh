@@ -47,46 +47,58 @@ HK_HD void vertex_vel(const MapGeo &m, int i, int j, int k, double C, double v[3
 }
 
 // volume, centroid and central second moments of cell (i,j,k) by the 2x2x2
-// Gauss rule on its trilinear map (weights 1/8 times |det J|)
+// Gauss rule on its trilinear map (weights 1/8 times |det J|).  The map
+// adds the same scalar D(p) = amp S sum_v psi_v(p) s_v to every coordinate
+// of the reference point xi_c + p h (p in [-1/2, 1/2]^3), so
+//   x - xi_c = p h + D (1,1,1),   J = diag(h) + (1,1,1) (grad_p D)^T,
+//   det J = h_x h_y h_z (1 + sum_e (dD/dp_e) / h_e)
+// (matrix determinant lemma); moments are taken about the reference centre
+// xi_c and shifted to the centroid.
 HK_HD void cell_geometry(const MapGeo &m, int i, int j, int k, double S, double out[NGEO])
 {
-    double hv[2][2][2][3];
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b)
-            for (int c = 0; c < 2; ++c) vertex_pos(m, i + a, j + b, k + c, S, hv[a][b][c]);
-    double X[8][3], w[8], vol = 0.0, m1[3] = {0, 0, 0};
-    int q = 0;
-    for (int ga = 0; ga < 2; ++ga)
-        for (int gb = 0; gb < 2; ++gb)
-            for (int gc = 0; gc < 2; ++gc, ++q) {
-                const double p[3] = {ga ? GAUSS_S : -GAUSS_S, gb ? GAUSS_S : -GAUSS_S, gc ? GAUSS_S : -GAUSS_S};
-                double x[3] = {0, 0, 0}, J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-                for (int a = 0; a < 2; ++a)
-                    for (int b = 0; b < 2; ++b)
-                        for (int c = 0; c < 2; ++c) {
-                            const double s[3] = {2.0 * a - 1.0, 2.0 * b - 1.0, 2.0 * c - 1.0};
-                            const double f0 = 0.5 * (1.0 + 2.0 * s[0] * p[0]);
-                            const double f1 = 0.5 * (1.0 + 2.0 * s[1] * p[1]);
-                            const double f2 = 0.5 * (1.0 + 2.0 * s[2] * p[2]);
-                            const double psi = f0 * f1 * f2;
-                            const double dpsi[3] = {s[0] * f1 * f2, f0 * s[1] * f2, f0 * f1 * s[2]};
-                            for (int d = 0; d < 3; ++d) {
-                                x[d] += hv[a][b][c][d] * psi;
-                                for (int e = 0; e < 3; ++e) J[d][e] += hv[a][b][c][d] * dpsi[e];
-                            }
-                        }
-                const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
-                                   J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
-                                   J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
-                w[q] = 0.125 * fabs(det);
-                for (int d = 0; d < 3; ++d) X[q][d] = x[d];
-                vol += w[q];
-                for (int d = 0; d < 3; ++d) m1[d] += w[q] * x[d];
-            }
-    double cen[3] = {m1[0] / vol, m1[1] / vol, m1[2] / vol};
+    const int idx[3] = {i, j, k};
+    double h[3], xc[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        h[e] = (m.hi[e] - m.lo[e]) / (double)m.n[e];
+        xc[e] = m.lo[e] + ((double)idx[e] + 0.5) * h[e];
+    }
+    const double aS = m.amp * S;
+    double sv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        sv[q] = m.sx[i + (q & 1) + 2] * m.sy[j + ((q >> 1) & 1) + 2] * m.sz[k + (q >> 2) + 2];
+    const double hprod = h[0] * h[1] * h[2];
+    double Y[8][3], w[8], vol = 0.0, m1[3] = {0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const double p[3] = {(q & 1) ? GAUSS_S : -GAUSS_S, ((q >> 1) & 1) ? GAUSS_S : -GAUSS_S,
+                             (q >> 2) ? GAUSS_S : -GAUSS_S};
+        const double lo[3] = {0.5 - p[0], 0.5 - p[1], 0.5 - p[2]};
+        const double hi[3] = {0.5 + p[0], 0.5 + p[1], 0.5 + p[2]};
+        double D = 0.0, gD[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            const int a = v & 1, b = (v >> 1) & 1, c = v >> 2;
+            const double f0 = a ? hi[0] : lo[0], f1 = b ? hi[1] : lo[1], f2 = c ? hi[2] : lo[2];
+            const double s0 = a ? 1.0 : -1.0, s1 = b ? 1.0 : -1.0, s2 = c ? 1.0 : -1.0;
+            D += f0 * f1 * f2 * sv[v];
+            gD[0] += s0 * f1 * f2 * sv[v];
+            gD[1] += f0 * s1 * f2 * sv[v];
+            gD[2] += f0 * f1 * s2 * sv[v];
+        }
+        D *= aS;
+        const double det = hprod * (1.0 + aS * (gD[0] / h[0] + gD[1] / h[1] + gD[2] / h[2]));
+        w[q] = 0.125 * fabs(det);
+        for (int d = 0; d < 3; ++d) Y[q][d] = p[d] * h[d] + D;
+        vol += w[q];
+        for (int d = 0; d < 3; ++d) m1[d] += w[q] * Y[q][d];
+    }
+    const double cy[3] = {m1[0] / vol, m1[1] / vol, m1[2] / vol};
     double M[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
     for (int r = 0; r < 8; ++r) {
-        const double dx = X[r][0] - cen[0], dy = X[r][1] - cen[1], dz = X[r][2] - cen[2];
+        const double dx = Y[r][0] - cy[0], dy = Y[r][1] - cy[1], dz = Y[r][2] - cy[2];
         M[0] += w[r] * dx * dx;
         M[1] += w[r] * dy * dy;
         M[2] += w[r] * dz * dz;
@@ -95,7 +107,7 @@ HK_HD void cell_geometry(const MapGeo &m, int i, int j, int k, double S, double 
         M[5] += w[r] * dy * dz;
     }
     out[0] = vol;
-    for (int d = 0; d < 3; ++d) out[1 + d] = cen[d];
+    for (int d = 0; d < 3; ++d) out[1 + d] = xc[d] + cy[d];
     for (int e = 0; e < 6; ++e) out[4 + e] = M[e] / vol;
 }
 
@@ -119,6 +131,22 @@ __device__ __forceinline__ void read_geo(const double *__restrict__ geo, const G
     const long long p = pidx(g, i, j, k);
 #pragma unroll
     for (int e = 0; e < NGEO; ++e) rec[e] = geo[e * g.pstride + p];
+}
+
+// centroid, h = |Omega|^(1/3) and the scaled second moments of cell (i,j,k)
+template <typename R>
+__device__ __forceinline__ void make_frame(const double *__restrict__ geo, const Geo &g, int i, int j, int k,
+                                           CellFrame<R> &F)
+{
+    double rec[NGEO];
+    read_geo(geo, g, i, j, k, rec);
+    F.c[0] = rec[1];
+    F.c[1] = rec[2];
+    F.c[2] = rec[3];
+    F.h = cbrt(rec[0]);
+    const double ih2 = 1.0 / (F.h * F.h);
+#pragma unroll
+    for (int e = 0; e < 6; ++e) F.Mh[e] = rec[4 + e] * ih2;
 }
 
 // row of the big-stencil system for the neighbour at offset o
@@ -363,7 +391,7 @@ __device__ __forceinline__ void pm_mapped_rt(const double *__restrict__ Qv, cons
 
 // literal positivity check (Sec. 4) on a trilinear cell
 template <typename R>
-__device__ __noinline__ bool positivity_violated_mapped(const double *__restrict__ Q, const double *__restrict__ geo,
+__device__ __forceinline__ bool positivity_violated_mapped(const double *__restrict__ Q, const double *__restrict__ geo,
                                                         const Geo &g, const MapGeo &m, double S, int i, int j, int k,
                                                         const CellFrame<R> &F, R gamma)
 {
@@ -397,110 +425,389 @@ __device__ __noinline__ bool positivity_violated_mapped(const double *__restrict
     return false;
 }
 
+// ---------------------------------------------------------------------------
+// Per-cell staging for the reconstruction: the 18 neighbours' centroid
+// offsets in the scaled frame, (c_nb - c)/h, formed once in FP64 and kept in
+// shared memory in the working precision; in the mixed path also the 90
+// differences Q_nb - Q_c (formed in FP64).  Each thread owns one column of
+// the block's array (stride RM_BS), so no synchronisation is needed.
+// ---------------------------------------------------------------------------
+constexpr int RM_BS = 64;  // threads per block of the reconstruction kernel
+template <typename R> struct RmStage {
+    static constexpr bool dq = sizeof(R) == 4;
+    static constexpr int n = 54 + (dq ? 90 : 0);
+};
+
+// offset of big-stencil neighbour s (0..17, the enumeration of big_offset)
+__device__ __forceinline__ void big_offset_rt(int s, int o[3])
+{
+    // skip the centre (13) and the corners (0, 2, 6, 8, 18, 20, 24, 26)
+    int p = s + 1;
+    p += p >= 2;
+    p += p >= 6;
+    p += p >= 8;
+    p += p >= 13;
+    p += p >= 18;
+    p += p >= 20;
+    p += p >= 24;
+    o[0] = p % 3 - 1;
+    o[1] = (p / 3) % 3 - 1;
+    o[2] = p / 9 - 1;
+}
+
+// index s of the big-stencil neighbour at offset o (inverse of big_offset_rt)
+__device__ __forceinline__ int big_index(const int o[3])
+{
+    const int p = (o[2] + 1) * 9 + (o[1] + 1) * 3 + (o[0] + 1);
+    return p - (p > 0) - (p > 2) - (p > 6) - (p > 8) - (p > 13) - (p > 18) - (p > 20) - (p > 24);
+}
+
+// row of the big-stencil system for neighbour s from the staged offsets and
+// the neighbour's second moments
+template <typename R>
+__device__ __forceinline__ void staged_row(const R *sh, const double *__restrict__ geo, const Geo &g, R ih2,
+                                           const R Mh[6], int s, long long pn, R row[9])
+{
+    const R D0 = sh[(3 * s + 0) * RM_BS], D1 = sh[(3 * s + 1) * RM_BS], D2 = sh[(3 * s + 2) * RM_BS];
+    R mm[6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) mm[e] = R(geo[(4 + e) * g.pstride + pn]) * ih2;
+    row[0] = D0;
+    row[1] = D1;
+    row[2] = D2;
+    row[3] = mm[0] - Mh[0] + D0 * D0;
+    row[4] = mm[1] - Mh[1] + D1 * D1;
+    row[5] = mm[2] - Mh[2] + D2 * D2;
+    row[6] = mm[3] - Mh[3] + D0 * D1;
+    row[7] = mm[4] - Mh[4] + D0 * D2;
+    row[8] = mm[5] - Mh[5] + D1 * D2;
+}
+
+// Q_nb - Q_c of variable v at big-stencil neighbour s
+template <typename R>
+__device__ __forceinline__ R staged_dq(const R *sh, const double *__restrict__ Q, const Geo &g, int v, int s,
+                                       long long pn, double qc)
+{
+    if constexpr (RmStage<R>::dq) return sh[(54 + 18 * v + s) * RM_BS];
+    else return R(Q[v * g.pstride + pn] - qc);
+}
+
+// the 8 vertices of cell (i,j,k), vertex (a,b,c) at V[a + 2b + 4c]
+__device__ __forceinline__ void cell_vertices(const MapGeo &m, int i, int j, int k, double S, double V[8][3])
+{
+#pragma unroll
+    for (int q = 0; q < 8; ++q) vertex_pos(m, i + (q & 1), j + ((q >> 1) & 1), k + (q >> 2), S, V[q]);
+}
+
+// face Gauss point gq of the cell with vertices V, in its scaled frame
+// (same points and order as cell_gauss_point)
+__device__ __forceinline__ void gauss_from_vertices(const double V[8][3], int gq, const double c[3], double h,
+                                                    double X[3])
+{
+    const int d = gq / 8, side = (gq / 4) & 1, ga = (gq >> 1) & 1, gb = gq & 1;
+    double p[3];
+    p[d] = side ? 0.5 : -0.5;
+    p[(d + 1) % 3] = ga ? GAUSS_S : -GAUSS_S;
+    p[(d + 2) % 3] = gb ? GAUSS_S : -GAUSS_S;
+    double x[3] = {0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int a = q & 1, b = (q >> 1) & 1, cc = q >> 2;
+        const double psi = 0.125 * (1.0 + 2.0 * (2 * a - 1) * p[0]) * (1.0 + 2.0 * (2 * b - 1) * p[1]) *
+                           (1.0 + 2.0 * (2 * cc - 1) * p[2]);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) x[e] += V[q][e] * psi;
+    }
+#pragma unroll
+    for (int e = 0; e < 3; ++e) X[e] = (x[e] - c[e]) / h;
+}
+
+// least-squares operator of sub-stencil M on a trilinear cell: b = P dq for
+// the data dq of its 4 cells, P = (R^T R)^{-1} R^T with R the 4 x 3 linear
+// rows; formed once per cell and applied to the five variables
+// offsets of the 4 cells of sub-stencil M for a run-time M, by selects
+// only (no run-time indexing of a local array)
+__device__ __forceinline__ void sub_offsets_rt(int M, int o[4][3])
+{
+    const int p = M >> 3, s = M & 7;
+    const int sa = (s & 1) ? -1 : 1, sb = (s & 2) ? -1 : 1, sc = (s & 4) ? -1 : 1;
+    // unit vectors of the axes a = p, b = p + 1, c = p + 2 (mod 3)
+    const int ea[3] = {p == 0, p == 1, p == 2};
+    const int eb[3] = {p == 2, p == 0, p == 1};
+    const int ec[3] = {p == 1, p == 2, p == 0};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        o[0][d] = sa * ea[d];
+        o[1][d] = sb * eb[d];
+        o[2][d] = sa * ea[d] + sb * eb[d];
+        o[3][d] = sc * ec[d];
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void sub_pinv(const R *sh, const int o[4][3], R P[3][4])
+{
+    R r[4][3];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int sq = big_index(o[q]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) r[q][d] = sh[(3 * sq + d) * RM_BS];
+    }
+    R G[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            R sum = R(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) sum += r[q][a] * r[q][b];
+            G[a][b] = sum;
+        }
+    // inverse of the symmetric 3 x 3 matrix by cofactors
+    const R c00 = G[1][1] * G[2][2] - G[1][2] * G[2][1];
+    const R c01 = G[1][2] * G[2][0] - G[1][0] * G[2][2];
+    const R c02 = G[1][0] * G[2][1] - G[1][1] * G[2][0];
+    const R c11 = G[0][0] * G[2][2] - G[0][2] * G[2][0];
+    const R c12 = G[0][2] * G[1][0] - G[0][0] * G[1][2];
+    const R c22 = G[0][0] * G[1][1] - G[0][1] * G[1][0];
+    const R idet = R(1) / (G[0][0] * c00 + G[0][1] * c01 + G[0][2] * c02);
+    const R Gi[3][3] = {{c00 * idet, c01 * idet, c02 * idet},
+                        {c01 * idet, c11 * idet, c12 * idet},
+                        {c02 * idet, c12 * idet, c22 * idet}};
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) P[d][q] = Gi[d][0] * r[q][0] + Gi[d][1] * r[q][1] + Gi[d][2] * r[q][2];
+}
+
+// differences Q_nb - Q_c of variable v over the 4 cells of a sub-stencil
+template <typename R>
+__device__ __forceinline__ void sub_dq(const R *sh, const double *__restrict__ Q, const Geo &g, int v, int i, int j,
+                                       int k, double qc, const int o[4][3], R dq[4])
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        dq[q] = staged_dq<R>(sh, Q, g, v, big_index(o[q]), pidx(g, i + o[q][0], j + o[q][1], k + o[q][2]), qc);
+}
+
+// sh: this thread's column of the block's staging array (RmStage<R>::n
+// entries, stride RM_BS)
 template <typename R>
 __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, const double *__restrict__ geo,
                                                   R *__restrict__ coef, unsigned char *__restrict__ flag,
                                                   const Geo &g, const MapGeo &m, double S, const Scheme &Sch, Ctl *ctl,
-                                                  long long t)
+                                                  R *sh, long long t)
 {
     if (t >= g.cstride) return;
     const int i = (int)(t % g.cx) - 1, j = (int)((t / g.cx) % g.cy) - 1, k = (int)(t / ((long long)g.cx * g.cy)) - 1;
     CellFrame<R> F;
-    {
-        double rec[NGEO];
-        read_geo(geo, g, i, j, k, rec);
-        F.c[0] = rec[1];
-        F.c[1] = rec[2];
-        F.c[2] = rec[3];
-        F.h = cbrt(rec[0]);
-        const double ih2 = 1.0 / (F.h * F.h);
-        for (int e = 0; e < 6; ++e) F.Mh[e] = rec[4 + e] * ih2;
-    }
+    make_frame(geo, g, i, j, k, F);
+    const double ih = 1.0 / F.h;
+    const R ih2 = R(ih * ih);
     const R Mh[6] = {R(F.Mh[0]), R(F.Mh[1]), R(F.Mh[2]), R(F.Mh[3]), R(F.Mh[4]), R(F.Mh[5])};
-    // extents of X and of the monomials over the cell's 24 face Gauss points,
-    // for the positivity bound
-    R ext[9];
-#pragma unroll
-    for (int n = 0; n < 9; ++n) ext[n] = R(0);
-#pragma unroll 1
-    for (int gq = 0; gq < 24; ++gq) {
-        double Xd[3];
-        cell_gauss_point(m, i, j, k, S, gq, F.c, F.h, Xd);
-        const R X[3] = {R(Xd[0]), R(Xd[1]), R(Xd[2])};
-        const R pn[9] = {X[0], X[1], X[2], X[0] * X[0] - Mh[0], X[1] * X[1] - Mh[1], X[2] * X[2] - Mh[2],
-                         X[0] * X[1] - Mh[3], X[0] * X[2] - Mh[4], X[1] * X[2] - Mh[5]};
-#pragma unroll
-        for (int n = 0; n < 9; ++n) ext[n] = m_max(ext[n], m_abs(pn[n]));
-    }
-    const R xmax = m_max(ext[0], m_max(ext[1], ext[2]));
-    // normal matrix of the big stencil, factored once for the 5 variables
-    R N[45];
-    normal_matrix_mapped<R>(geo, g, F, i, j, k, N);
-
     const R g0 = R(1.0 - 24.0 * Sch.Gamma_lin), gm = R(Sch.Gamma_lin), eps = R(Sch.weno_eps);
     const R ig0 = R(1) / g0;
-    R rad[5], qcv[5];
-#pragma unroll 1
-    for (int v = 0; v < 5; ++v) {
-        const double *Qv = Q + v * g.pstride;
-        const double qc = Qv[pidx(g, i, j, k)];
-        qcv[v] = R(qc);
-        R a[9];
-        p0_mapped<R>(Qv, geo, g, F, N, i, j, k, qc, a);
-        const R beta0 = beta_quadratic_mapped(a, Mh);
-        R tau = R(0);
-        R bsum = R(0);  // largest |b_x| + |b_y| + |b_z| over the P_m
-#define HK_MP1(M)                                                 \
-    {                                                             \
-        R b[3];                                                   \
-        pm_mapped<M, R>(Qv, geo, g, F, i, j, k, qc, b);           \
-        const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];     \
-        tau += m_abs(beta0 - bm);                                 \
-        bsum = m_max(bsum, m_abs(b[0]) + m_abs(b[1]) + m_abs(b[2])); \
-    }
-        HK_FOR_SUBSTENCILS(HK_MP1)
-#undef HK_MP1
-        tau *= R(1.0 / 24.0);
-        const R x0 = tau / (beta0 + eps);
-        const R w0 = g0 * (R(1) + (Sch.weno_pow == 2 ? x0 * x0 : x0));
-        R wsum = w0;
-        R lin[3] = {R(0), R(0), R(0)};
-#define HK_MP2(M)                                                 \
-    {                                                             \
-        R b[3];                                                   \
-        pm_mapped<M, R>(Qv, geo, g, F, i, j, k, qc, b);           \
-        const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];     \
-        const R xm = tau / (bm + eps);                            \
-        const R wm = gm * (R(1) + (Sch.weno_pow == 2 ? xm * xm : xm)); \
-        wsum += wm;                                               \
-        const R cm = wm - w0 * gm * ig0;                          \
-        lin[0] += cm * b[0];                                      \
-        lin[1] += cm * b[1];                                      \
-        lin[2] += cm * b[2];                                      \
-    }
-        HK_FOR_SUBSTENCILS(HK_MP2)
-#undef HK_MP2
-        const R iw = R(1) / wsum;
-        const R f0 = w0 * ig0;
-        coef[coef_slot(v, 0) * g.cstride + t] = R(qc);
+    const bool pow2 = Sch.weno_pow == 2;
+    const long long pc = pidx(g, i, j, k);
+    double qcd[5];
+    R qcv[5];
 #pragma unroll
-        for (int n = 0; n < 9; ++n)
-            coef[coef_slot(v, 1 + n) * g.cstride + t] = iw * (f0 * a[n] + (n < 3 ? lin[n] : R(0)));
-        // rigorous bound of |P_m - Q_c| at the Gauss points for all 25 P_m
+    for (int v = 0; v < 5; ++v) {
+        qcd[v] = Q[v * g.pstride + pc];
+        qcv[v] = R(qcd[v]);
+    }
+    // stage the neighbours' scaled centroid offsets (and, mixed, the data
+    // differences)
+#pragma unroll 1
+    for (int s = 0; s < 18; ++s) {
+        int o[3];
+        big_offset_rt(s, o);
+        const long long pn = pidx(g, i + o[0], j + o[1], k + o[2]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sh[(3 * s + d) * RM_BS] = R((geo[(1 + d) * g.pstride + pn] - F.c[d]) * ih);
+        if constexpr (RmStage<R>::dq) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) sh[(54 + 18 * v + s) * RM_BS] = R(Q[v * g.pstride + pn] - qcd[v]);
+        }
+    }
+
+    // P0 of every variable with the big stencil's normal matrix, factored
+    // once; beta0 and the coefficients are parked in the output slots (0 and
+    // 1..9 of each variable) until the weights are known
+    {
+        R N[45];
+#pragma unroll
+        for (int e = 0; e < 45; ++e) N[e] = R(0);
+#pragma unroll 1
+        for (int s = 0; s < 18; ++s) {
+            int o[3];
+            big_offset_rt(s, o);
+            R row[9];
+            staged_row<R>(sh, geo, g, ih2, Mh, s, pidx(g, i + o[0], j + o[1], k + o[2]), row);
+#pragma unroll
+            for (int a = 0; a < 9; ++a)
+#pragma unroll
+                for (int b = 0; b <= a; ++b) N[a * (a + 1) / 2 + b] += row[a] * row[b];
+        }
+        chol_factor<R, 9>(N);
+#pragma unroll 1
+        for (int v = 0; v < 5; ++v) {
+            const double qc = Q[v * g.pstride + pc];
+            R a[9];
+#pragma unroll
+            for (int n = 0; n < 9; ++n) a[n] = R(0);
+#pragma unroll 1
+            for (int s = 0; s < 18; ++s) {
+                int o[3];
+                big_offset_rt(s, o);
+                const long long pn = pidx(g, i + o[0], j + o[1], k + o[2]);
+                R row[9];
+                staged_row<R>(sh, geo, g, ih2, Mh, s, pn, row);
+                const R dq = staged_dq<R>(sh, Q, g, v, s, pn, qc);
+#pragma unroll
+                for (int n = 0; n < 9; ++n) a[n] += row[n] * dq;
+            }
+            chol_solve<R, 9>(N, a);
+            coef[coef_slot(v, 0) * g.cstride + t] = beta_quadratic_mapped(a, Mh);
+#pragma unroll
+            for (int n = 0; n < 9; ++n) coef[coef_slot(v, 1 + n) * g.cstride + t] = a[n];
+        }
+    }
+    R beta0[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) beta0[v] = coef[coef_slot(v, 0) * g.cstride + t];
+    // sub-stencils, first pass: tau = mean |beta0 - beta_m| and the largest
+    // |b_x| + |b_y| + |b_z| over the P_m (positivity bound)
+    R tau[5], bsum[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) tau[v] = bsum[v] = R(0);
+#pragma unroll 1
+    for (int M = 0; M < 24; ++M) {
+        int o[4][3];
+        sub_offsets_rt(M, o);
+        R P[3][4];
+        sub_pinv<R>(sh, o, P);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            R dq[4];
+            sub_dq<R>(sh, Q, g, v, i, j, k, qcd[v], o, dq);
+            R b[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) b[d] = P[d][0] * dq[0] + P[d][1] * dq[1] + P[d][2] * dq[2] + P[d][3] * dq[3];
+            const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+            tau[v] += m_abs(beta0[v] - bm);
+            bsum[v] = m_max(bsum[v], m_abs(b[0]) + m_abs(b[1]) + m_abs(b[2]));
+        }
+    }
+    // second pass: nonlinear weights and the linear part of P~
+    R w0[5], wsum[5], lin[5][3];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        tau[v] *= R(1.0 / 24.0);
+        const R x0 = tau[v] / (beta0[v] + eps);
+        w0[v] = g0 * (R(1) + (pow2 ? x0 * x0 : x0));
+        wsum[v] = w0[v];
+        lin[v][0] = lin[v][1] = lin[v][2] = R(0);
+    }
+#pragma unroll 1
+    for (int M = 0; M < 24; ++M) {
+        int o[4][3];
+        sub_offsets_rt(M, o);
+        R P[3][4];
+        sub_pinv<R>(sh, o, P);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+            R dq[4];
+            sub_dq<R>(sh, Q, g, v, i, j, k, qcd[v], o, dq);
+            R b[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) b[d] = P[d][0] * dq[0] + P[d][1] * dq[1] + P[d][2] * dq[2] + P[d][3] * dq[3];
+            const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+            const R xm = tau[v] / (bm + eps);
+            const R wm = gm * (R(1) + (pow2 ? xm * xm : xm));
+            wsum[v] += wm;
+            const R cm = wm - w0[v] * gm * ig0;
+            lin[v][0] += cm * b[0];
+            lin[v][1] += cm * b[1];
+            lin[v][2] += cm * b[2];
+        }
+    }
+    // extents of X and of the monomials over the cell's 24 face Gauss
+    // points, for the positivity bound.  Every coordinate of a point is
+    // displaced by the same amp S sum_v psi_v s_v (trilinear weights psi_v,
+    // vertex sine products s_v), so in the scaled frame
+    //   X_e = (xi_centre,e - c_e)/h + p_e h_e/h + (amp S/h) sum_v psi_v s_v
+    // for the point's reference offset p in [-1/2, 1/2]^3.
+    R ext[9];
+    {
+        R sv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            sv[q] = R(m.sx[i + (q & 1) + 2]) * R(m.sy[j + ((q >> 1) & 1) + 2]) * R(m.sz[k + (q >> 2) + 2]);
+        const int idx[3] = {i, j, k};
+        R x0[3], hr[3];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            const double he = (m.hi[e] - m.lo[e]) / (double)m.n[e];
+            x0[e] = R((m.lo[e] + ((double)idx[e] + 0.5) * he - F.c[e]) * ih);
+            hr[e] = R(he * ih);
+        }
+        const R aSh = R(m.amp * S * ih);
+#pragma unroll
+        for (int n = 0; n < 9; ++n) ext[n] = R(0);
+#pragma unroll 1
+        for (int gq = 0; gq < 24; ++gq) {
+            const int d = gq / 8, side = (gq / 4) & 1, ga = (gq >> 1) & 1, gb = gq & 1;
+            R p[3];
+            p[0] = p[1] = p[2] = R(0);
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                const int rel = (e - d + 3) % 3;  // 0: face normal, 1: first tangent, 2: second
+                p[e] = rel == 0 ? (side ? R(0.5) : R(-0.5))
+                                : (rel == 1 ? (ga ? R(GAUSS_S) : R(-GAUSS_S)) : (gb ? R(GAUSS_S) : R(-GAUSS_S)));
+            }
+            R wlo[3], whi[3];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                wlo[e] = R(0.5) - p[e];
+                whi[e] = R(0.5) + p[e];
+            }
+            R dsum = R(0);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                dsum += ((q & 1) ? whi[0] : wlo[0]) * (((q >> 1) & 1) ? whi[1] : wlo[1]) *
+                        ((q >> 2) ? whi[2] : wlo[2]) * sv[q];
+            const R dd = aSh * dsum;
+            const R X[3] = {x0[0] + p[0] * hr[0] + dd, x0[1] + p[1] * hr[1] + dd, x0[2] + p[2] * hr[2] + dd};
+            const R pn[9] = {X[0], X[1], X[2], X[0] * X[0] - Mh[0], X[1] * X[1] - Mh[1], X[2] * X[2] - Mh[2],
+                             X[0] * X[1] - Mh[3], X[0] * X[2] - Mh[4], X[1] * X[2] - Mh[5]};
+#pragma unroll
+            for (int n = 0; n < 9; ++n) ext[n] = m_max(ext[n], m_abs(pn[n]));
+        }
+    }
+    const R xmax = m_max(ext[0], m_max(ext[1], ext[2]));
+    R rad[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        const R iw = R(1) / wsum[v];
+        const R f0 = w0[v] * ig0;
+        coef[coef_slot(v, 0) * g.cstride + t] = qcv[v];
         R r0 = R(0);
 #pragma unroll
-        for (int n = 0; n < 9; ++n) r0 += m_abs(a[n]) * ext[n];
-        rad[v] = m_max(r0, bsum * xmax) * R(1.0000001);
+        for (int n = 0; n < 9; ++n) {
+            R *cp = coef + coef_slot(v, 1 + n) * g.cstride + t;
+            const R a = *cp;
+            r0 += m_abs(a) * ext[n];
+            *cp = iw * (f0 * a + (n < 3 ? lin[v][n] : R(0)));
+        }
+        // bound of |P_m - Q_c| at the Gauss points for all 25 P_m
+        rad[v] = m_max(r0, bsum[v] * xmax) * R(1.0000001);
     }
-    bool bad = false;
-    if (Sch.limiter && !positivity_certain(qcv, rad, R(Sch.gamma)))
-        bad = positivity_violated_mapped<R>(Q, geo, g, m, S, i, j, k, F, R(Sch.gamma));
-    if (bad) {
-        for (int v = 0; v < 5; ++v)
-            for (int n = 1; n < 10; ++n) coef[coef_slot(v, n) * g.cstride + t] = R(0);
-        atomicAdd(&ctl->flagged, 1);
-    }
-    flag[t] = bad ? 1 : 0;
+    // a cell whose bound does not certify positivity is marked 2 and gets
+    // the literal check in positivity_mapped_item (a kernel of its own, so
+    // that its registers do not weigh on this one)
+    flag[t] = (Sch.limiter && !positivity_certain(qcv, rad, R(Sch.gamma))) ? 2 : 0;
     // the cell frame for the flux kernels
     coef[(SLOT_FRAME + 0) * g.cstride + t] = R(F.c[0]);
     coef[(SLOT_FRAME + 1) * g.cstride + t] = R(F.c[1]);
@@ -508,6 +815,28 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
     coef[(SLOT_FRAME + 3) * g.cstride + t] = R(F.h);
 #pragma unroll
     for (int e = 0; e < 6; ++e) coef[(SLOT_FRAME + 4 + e) * g.cstride + t] = Mh[e];
+}
+
+// literal positivity check of the cells marked 2 by recon_mapped_item: all
+// 25 polynomials at the cell's 24 face Gauss points; a violation sets P~ to
+// the cell average (Sec. 4)
+template <typename R>
+__device__ __forceinline__ void positivity_mapped_item(const double *__restrict__ Q, const double *__restrict__ geo,
+                                                       R *__restrict__ coef, unsigned char *__restrict__ flag,
+                                                       const Geo &g, const MapGeo &m, double S, const Scheme &Sch,
+                                                       Ctl *ctl, long long t)
+{
+    if (t >= g.cstride || flag[t] != 2) return;
+    const int i = (int)(t % g.cx) - 1, j = (int)((t / g.cx) % g.cy) - 1, k = (int)(t / ((long long)g.cx * g.cy)) - 1;
+    CellFrame<R> F;
+    make_frame(geo, g, i, j, k, F);
+    const bool bad = positivity_violated_mapped<R>(Q, geo, g, m, S, i, j, k, F, R(Sch.gamma));
+    if (bad) {
+        for (int v = 0; v < 5; ++v)
+            for (int n = 1; n < 10; ++n) coef[coef_slot(v, n) * g.cstride + t] = R(0);
+        atomicAdd(&ctl->flagged, 1);
+    }
+    flag[t] = bad ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -520,7 +849,7 @@ constexpr int NFACE_M = 11;
 
 template <typename R>
 __device__ __forceinline__ void eval_cell_mapped(const R *__restrict__ coef, const Geo &g, long long ci,
-                                                 const double xg[3], R val[5], R grad[5][3])
+                                                 const R xg[3], R val[5], R grad[5][3])
 {
     R c[3], h, Mh[6];
 #pragma unroll
@@ -529,7 +858,7 @@ __device__ __forceinline__ void eval_cell_mapped(const R *__restrict__ coef, con
 #pragma unroll
     for (int e = 0; e < 6; ++e) Mh[e] = coef[(SLOT_FRAME + 4 + e) * g.cstride + ci];
     const R ih = R(1) / h;
-    const R X[3] = {(R(xg[0]) - c[0]) * ih, (R(xg[1]) - c[1]) * ih, (R(xg[2]) - c[2]) * ih};
+    const R X[3] = {(xg[0] - c[0]) * ih, (xg[1] - c[1]) * ih, (xg[2] - c[2]) * ih};
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
         R a[9];
@@ -542,9 +871,20 @@ __device__ __forceinline__ void eval_cell_mapped(const R *__restrict__ coef, con
     }
 }
 
+// The map displaces every coordinate of a vertex by the same scalar
+// amp S(t) s_v (s_v the product of the vertex's sine factors) and moves it
+// with velocity amp omega C(t) s_v in every coordinate.  On the bilinear face
+// spanned by the reference edges h_A e_A and h_B e_B this gives, at face
+// parameters (1/2 + ea, 1/2 + eb):
+//   X   = xi + d (1,1,1),          d  = amp S sum_v phi_v s_v
+//   X_a = h_A e_A + dA (1,1,1),    dA = amp S sum_v dphi_v/da s_v
+//   X_b = h_B e_B + dB (1,1,1),    dB = amp S sum_v dphi_v/db s_v
+//   U_g = ug (1,1,1),              ug = amp omega C sum_v phi_v s_v
+// so the face geometry needs only the 4 sine products, in the working
+// precision.
 template <typename R, int D>
 __device__ __forceinline__ void flux_mapped_item(const R *__restrict__ coef, double *__restrict__ Fout, const Geo &g,
-                                                 const MapGeo &m, double t_stage, const Scheme &S, double dt,
+                                                 const MapGeo &m, double Sf, double Cf, const Scheme &S, double dt,
                                                  long long t)
 {
     const int ex = g.nx + (D == 0), ey = g.ny + (D == 1);
@@ -556,41 +896,43 @@ __device__ __forceinline__ void flux_mapped_item(const R *__restrict__ coef, dou
     const int i = (int)(face % ex), j = (int)((face / ex) % ey), k = (int)(face / ((long long)ex * ey));
     const int il = i - (D == 0), jl = j - (D == 1), kl = k - (D == 2);
     constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
-    const double Sf = map_factor(m, t_stage);
-    const double Cf = m.moving ? cos(m.omega * t_stage) : 0.0;
-    const double ea = (gp & 2) ? GAUSS_S : -GAUSS_S, eb = (gp & 1) ? GAUSS_S : -GAUSS_S;
-    // bilinear face through the 4 vertices (i,j,k) + {0,1} e_A + {0,1} e_B
-    double X[3] = {0, 0, 0}, Xa[3] = {0, 0, 0}, Xb[3] = {0, 0, 0}, Vg[3] = {0, 0, 0};
+    const R ea = (gp & 2) ? R(GAUSS_S) : R(-GAUSS_S), eb = (gp & 1) ? R(GAUSS_S) : R(-GAUSS_S);
+    R sphi = R(0), spa = R(0), spb = R(0);
 #pragma unroll
     for (int sa = 0; sa < 2; ++sa)
 #pragma unroll
         for (int sb = 0; sb < 2; ++sb) {
-            int o[3] = {0, 0, 0};
-            o[A] = sa;
-            o[B] = sb;
-            double v[3], u[3];
-            vertex_pos(m, i + o[0], j + o[1], k + o[2], Sf, v);
-            vertex_vel(m, i + o[0], j + o[1], k + o[2], Cf, u);
-            const double qa = 2.0 * sa - 1.0, qb = 2.0 * sb - 1.0;
-            const double phi = 0.25 * (1.0 + 2.0 * qa * ea) * (1.0 + 2.0 * qb * eb);
-            const double pa = 0.5 * qa * (1.0 + 2.0 * qb * eb);
-            const double pb = 0.5 * qb * (1.0 + 2.0 * qa * ea);
-#pragma unroll
-            for (int e = 0; e < 3; ++e) {
-                X[e] += v[e] * phi;
-                Xa[e] += v[e] * pa;
-                Xb[e] += v[e] * pb;
-                Vg[e] += u[e] * phi;
-            }
+            int o[3] = {i, j, k};
+            o[A] += sa;
+            o[B] += sb;
+            const R sv = R(m.sx[o[0] + 2]) * R(m.sy[o[1] + 2]) * R(m.sz[o[2] + 2]);
+            const R qa = R(2 * sa - 1), qb = R(2 * sb - 1);
+            sphi += R(0.25) * (R(1) + R(2) * qa * ea) * (R(1) + R(2) * qb * eb) * sv;
+            spa += R(0.5) * qa * (R(1) + R(2) * qb * eb) * sv;
+            spb += R(0.5) * qb * (R(1) + R(2) * qa * ea) * sv;
         }
-    const double nrm[3] = {Xa[1] * Xb[2] - Xa[2] * Xb[1], Xa[2] * Xb[0] - Xa[0] * Xb[2], Xa[0] * Xb[1] - Xa[1] * Xb[0]};
-    const double area = sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
-    const double lb = sqrt(Xb[0] * Xb[0] + Xb[1] * Xb[1] + Xb[2] * Xb[2]);
-    double fr[3][3];
+    const R aS = R(m.amp * Sf);
+    const R d = aS * sphi, dA = aS * spa, dB = aS * spb;
+    const R ug = m.moving ? R(m.amp * m.omega * Cf) * sphi : R(0);
+    const int idx[3] = {i, j, k};
+    R X[3], Xa[3], Xb[3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-        fr[0][e] = nrm[e] / area;
-        fr[2][e] = Xb[e] / lb;
+        const double he = (m.hi[e] - m.lo[e]) / (double)m.n[e];
+        const double par = e == D ? 0.0 : (e == A ? 0.5 + (double)ea : 0.5 + (double)eb);
+        X[e] = R(m.lo[e] + ((double)idx[e] + par) * he) + d;
+        Xa[e] = (e == A ? R(he) : R(0)) + dA;
+        Xb[e] = (e == B ? R(he) : R(0)) + dB;
+    }
+    const R nrm[3] = {Xa[1] * Xb[2] - Xa[2] * Xb[1], Xa[2] * Xb[0] - Xa[0] * Xb[2], Xa[0] * Xb[1] - Xa[1] * Xb[0]};
+    const R area = m_sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+    const R iarea = R(1) / area;
+    const R ilb = R(1) / m_sqrt(Xb[0] * Xb[0] + Xb[1] * Xb[1] + Xb[2] * Xb[2]);
+    R fr[3][3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        fr[0][e] = nrm[e] * iarea;
+        fr[2][e] = Xb[e] * ilb;
     }
     fr[1][0] = fr[2][1] * fr[0][2] - fr[2][2] * fr[0][1];
     fr[1][1] = fr[2][2] * fr[0][0] - fr[2][0] * fr[0][2];
@@ -601,9 +943,7 @@ __device__ __forceinline__ void flux_mapped_item(const R *__restrict__ coef, dou
     for (int s = 0; s < 2; ++s) {
         R val[5], grad[5][3];
         eval_cell_mapped<R>(coef, g, s ? cidx(g, i, j, k) : cidx(g, il, jl, kl), X, val, grad);
-        const R f[3][3] = {{R(fr[0][0]), R(fr[0][1]), R(fr[0][2])},
-                           {R(fr[1][0]), R(fr[1][1]), R(fr[1][2])},
-                           {R(fr[2][0]), R(fr[2][1]), R(fr[2][2])}};
+        const R(&f)[3][3] = fr;
         Wc[s][0] = val[0];
         Wc[s][4] = val[4];
 #pragma unroll
@@ -622,7 +962,7 @@ __device__ __forceinline__ void flux_mapped_item(const R *__restrict__ coef, dou
     // the frame moving with the grid (Remark 2): shift the states by U_g
     R Ug[3];
 #pragma unroll
-    for (int l = 0; l < 3; ++l) Ug[l] = R(Vg[0] * fr[l][0] + Vg[1] * fr[l][1] + Vg[2] * fr[l][2]);
+    for (int l = 0; l < 3; ++l) Ug[l] = ug * (fr[l][0] + fr[l][1] + fr[l][2]);
     const R u2 = Ug[0] * Ug[0] + Ug[1] * Ug[1] + Ug[2] * Ug[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
@@ -651,7 +991,7 @@ __device__ __forceinline__ void flux_mapped_item(const R *__restrict__ coef, dou
     }
     Fb[4] = Fl[4] + Ug[0] * Fl[1] + Ug[1] * Fl[2] + Ug[2] * Fl[3] + R(0.5) * u2 * Fl[0];
     dFb[4] = dFl[4] + Ug[0] * dFl[1] + Ug[1] * dFl[2] + Ug[2] * dFl[3] + R(0.5) * u2 * dFl[0];
-    const R wgt = R(0.25 * area);
+    const R wgt = R(0.25) * area;
     R f[NFACE_M];
     f[0] = wgt * Fb[0];
     f[4] = wgt * Fb[4];
@@ -660,10 +1000,10 @@ __device__ __forceinline__ void flux_mapped_item(const R *__restrict__ coef, dou
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
         // the frame is orthonormal: its inverse is its transpose
-        f[1 + e] = wgt * (R(fr[0][e]) * Fb[1] + R(fr[1][e]) * Fb[2] + R(fr[2][e]) * Fb[3]);
-        f[6 + e] = wgt * (R(fr[0][e]) * dFb[1] + R(fr[1][e]) * dFb[2] + R(fr[2][e]) * dFb[3]);
+        f[1 + e] = wgt * (fr[0][e] * Fb[1] + fr[1][e] * Fb[2] + fr[2][e] * Fb[3]);
+        f[6 + e] = wgt * (fr[0][e] * dFb[1] + fr[1][e] * dFb[2] + fr[2][e] * dFb[3]);
     }
-    f[10] = R(0.25 * (Vg[0] * nrm[0] + Vg[1] * nrm[1] + Vg[2] * nrm[2]));
+    f[10] = R(0.25) * ug * (nrm[0] + nrm[1] + nrm[2]);
 #pragma unroll
     for (int q = 0; q < NFACE_M; ++q) {
         f[q] += __shfl_xor_sync(0xffffffffu, f[q], 1);

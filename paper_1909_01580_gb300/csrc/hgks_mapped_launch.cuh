@@ -6,7 +6,7 @@ namespace hk {
 
 struct MapGeo;
 
-void launch_geom(double *geo, const Geo &g, const MapGeo &m, const Ctl *ctl, int half, double t_fixed,
+void launch_geom(double *geo, const Geo &g, const MapGeo &m, Ctl *ctl, int half, double t_fixed,
                  cudaStream_t s);
 void launch_vol_from_geo(const double *geo, double *vol, const Geo &g, cudaStream_t s);
 template <typename R>
