@@ -26,6 +26,13 @@ HK_HD double m_erfc(double x) { return erfc(x); }
 HK_HD float m_erfc(float x) { return erfcf(x); }
 HK_HD double m_sqrt(double x) { return sqrt(x); }
 HK_HD float m_sqrt(float x) { return sqrtf(x); }
+#ifdef __CUDA_ARCH__
+HK_HD double m_rsqrt(double x) { return rsqrt(x); }
+HK_HD float m_rsqrt(float x) { return rsqrtf(x); }
+#else
+HK_HD double m_rsqrt(double x) { return 1.0 / sqrt(x); }
+HK_HD float m_rsqrt(float x) { return 1.0f / sqrtf(x); }
+#endif
 HK_HD double m_abs(double x) { return fabs(x); }
 HK_HD double m_max(double a, double b) { return fmax(a, b); }
 HK_HD float m_max(float a, float b) { return fmaxf(a, b); }
@@ -90,11 +97,6 @@ struct Ctl {
 // <u^{n+2}> = U <u^{n+1}> + (n+1)/(2 lam) <u^n>, on the whole line and on
 // either half line (the boundary term vanishes for n >= 1 at u = 0).
 // ---------------------------------------------------------------------------
-template <typename R> struct Mom {
-    R u[7], v[7], w[7];
-    R xi2, xi4;
-};
-
 template <typename R>
 HK_HD void mom_full_1d(R U, R th, R *m)
 {
@@ -110,114 +112,151 @@ template <typename R>
 HK_HD void mom_half_1d(R U, R lam, R th, R side, R *m)
 {
     const R inv_sqrt_pi = R(0.56418958354775628695);
-    R sl = m_sqrt(lam);
-    m[0] = R(0.5) * m_erfc(-side * sl * U);
-    m[1] = U * m[0] + side * R(0.5) * inv_sqrt_pi * m_exp(-lam * U * U) / sl;
+    const R isl = m_rsqrt(lam);
+    m[0] = R(0.5) * m_erfc(-side * (lam * isl) * U);
+    m[1] = U * m[0] + side * R(0.5) * inv_sqrt_pi * m_exp(-lam * U * U) * isl;
 #pragma unroll
     for (int n = 2; n < 7; ++n) m[n] = U * m[n - 1] + R(n - 1) * th * m[n - 2];
 }
 
-template <int A, int B, int C, typename R> HK_HD R M3(const Mom<R> &m)
+// ---------------------------------------------------------------------------
+// Moments in the frame moving with a Maxwellian's tangential velocity.
+// With v' = v - V and w' = w - W the tangential velocities are central
+// Gaussians (odd moments vanish, <v'^2> = <w'^2> = th = 1/(2 lam)), and
+// psi = T psi' for psi' = (1, u, v', w', E'), E' = (u^2 + r)/2,
+// r = v'^2 + w'^2 + xi^2, with
+//   T x' = (x'0, x'1, x'2 + V x'0, x'3 + W x'0,
+//           x'4 + V x'2 + W x'3 + (V^2 + W^2)/2 x'0).
+// A slope a (a . psi) becomes a' = T^T a, found directly from the
+// transformed moment data b' = T^{-1} b.  Moments in u stay as they are
+// (whole or half line), m[n] = <u^n>, n = 0..6.
+// ---------------------------------------------------------------------------
+template <typename R> struct BMom {
+    R m[7];
+    R th;  // <v'^2> = <w'^2>
+    R r1;  // <r>      = (K + 2) th
+    R r2;  // <r^2>    = (K + 2)(K + 4) th^2
+    R vr;  // <v'^2 r> = (K + 4) th^2
+};
+
+template <typename R> HK_HD void bmom_tangential(BMom<R> &B, R th, R K)
 {
-    return m.u[A] * m.v[B] * m.w[C];
+    B.th = th;
+    B.r1 = (K + R(2)) * th;
+    B.vr = (K + R(4)) * th * th;
+    B.r2 = (K + R(2)) * B.vr;
 }
 
-// <u^A v^B w^C psi>, psi = (1, u, v, w, (u^2 + v^2 + w^2 + xi^2)/2)
-template <int A, int B, int C, typename R> HK_HD void psi_m(const Mom<R> &m, R o[5])
+// x = T x' (in place)
+template <typename R> HK_HD void boost_out(R V, R W, R x[5])
 {
-    R m0 = M3<A, B, C>(m);
-    o[0] = m0;
-    o[1] = M3<A + 1, B, C>(m);
-    o[2] = M3<A, B + 1, C>(m);
-    o[3] = M3<A, B, C + 1>(m);
-    o[4] = R(0.5) * (M3<A + 2, B, C>(m) + M3<A, B + 2, C>(m) + M3<A, B, C + 2>(m) + m.xi2 * m0);
+    x[4] += V * x[2] + W * x[3] + R(0.5) * (V * V + W * W) * x[0];
+    x[2] += V * x[0];
+    x[3] += W * x[0];
 }
 
-// <xi^2 u^A v^B w^C psi>
-template <int A, int B, int C, typename R> HK_HD void psi_xi_m(const Mom<R> &m, R o[5])
+// b' = T^{-1} b (in place)
+template <typename R> HK_HD void boost_in(R V, R W, R b[5])
 {
-    R m0 = M3<A, B, C>(m);
-    o[0] = m.xi2 * m0;
-    o[1] = m.xi2 * M3<A + 1, B, C>(m);
-    o[2] = m.xi2 * M3<A, B + 1, C>(m);
-    o[3] = m.xi2 * M3<A, B, C + 1>(m);
-    o[4] = R(0.5) * (m.xi2 * (M3<A + 2, B, C>(m) + M3<A, B + 2, C>(m) + M3<A, B, C + 2>(m)) + m.xi4 * m0);
+    b[2] -= V * b[0];
+    b[3] -= W * b[0];
+    b[4] -= V * b[2] + W * b[3] + R(0.5) * (V * V + W * W) * b[0];
 }
 
-// <(s . psi) u^A v^B w^C psi>
-template <int A, int B, int C, typename R>
-HK_HD void apsi_m(const Mom<R> &m, const R s[5], R o[5])
+// <u^n psi'>
+template <int N, typename R> HK_HD void bpsi(const BMom<R> &B, R o[5])
 {
-    R t[5], q[5];
-    psi_m<A, B, C>(m, t);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) o[k] = s[0] * t[k];
-    psi_m<A + 1, B, C>(m, t);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) o[k] += s[1] * t[k];
-    psi_m<A, B + 1, C>(m, t);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) o[k] += s[2] * t[k];
-    psi_m<A, B, C + 1>(m, t);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) o[k] += s[3] * t[k];
-    psi_m<A + 2, B, C>(m, q);
-    psi_m<A, B + 2, C>(m, t);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) q[k] += t[k];
-    psi_m<A, B, C + 2>(m, t);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) q[k] += t[k];
-    psi_xi_m<A, B, C>(m, t);
-#pragma unroll
-    for (int k = 0; k < 5; ++k) o[k] += R(0.5) * s[4] * (q[k] + t[k]);
+    o[0] = B.m[N];
+    o[1] = B.m[N + 1];
+    o[2] = o[3] = R(0);
+    o[4] = R(0.5) * (B.m[N + 2] + B.r1 * B.m[N]);
 }
 
-// Solve <(a . psi) psi> = b (moments per unit density) in closed form for a
-// Maxwellian with velocity (U, V, W) and lam, written in the peculiar
-// velocity: the moment matrix is block-structured there.
-template <typename R>
-HK_HD void micro_slope(R U, R V, R W, R lam, R Kp3, const R b[5], R a[5])
+// <u^n (c . psi') psi'>
+template <int N, typename R> HK_HD void bapsi(const BMom<R> &B, const R c[5], R o[5])
 {
-    R q2 = U * U + V * V + W * W + Kp3 / (R(2) * lam);
-    R r4 = R(2) * b[4] - q2 * b[0];
-    R r1 = b[1] - U * b[0];
-    R r2 = b[2] - V * b[0];
-    R r3 = b[3] - W * b[0];
-    a[4] = R(4) * lam * lam / Kp3 * (r4 - R(2) * (U * r1 + V * r2 + W * r3));
-    a[1] = R(2) * lam * r1 - U * a[4];
-    a[2] = R(2) * lam * r2 - V * a[4];
-    a[3] = R(2) * lam * r3 - W * a[4];
-    a[0] = b[0] - U * a[1] - V * a[2] - W * a[3] - R(0.5) * a[4] * q2;
+    const R *m = B.m;
+    const R e0 = m[N + 2] + B.r1 * m[N];          // 2 <u^n E'>
+    const R e1 = m[N + 3] + B.r1 * m[N + 1];      // 2 <u^{n+1} E'>
+    const R e2 = m[N + 4] + R(2) * B.r1 * m[N + 2] + B.r2 * m[N];  // 4 <u^n E'^2>
+    const R h4 = R(0.5) * c[4];
+    o[0] = c[0] * m[N] + c[1] * m[N + 1] + h4 * e0;
+    o[1] = c[0] * m[N + 1] + c[1] * m[N + 2] + h4 * e1;
+    o[2] = c[2] * B.th * m[N];
+    o[3] = c[3] * B.th * m[N];
+    o[4] = R(0.5) * (c[0] * e0 + c[1] * e1 + h4 * e2);
+}
+
+// <u^n v' (c . psi') psi'> (T = 0) or <u^n w' (c . psi') psi'> (T = 1)
+template <int N, int T, typename R> HK_HD void bapsi_t(const BMom<R> &B, const R c[5], R o[5])
+{
+    const R *m = B.m;
+    const R ct = T ? c[3] : c[2];
+    const R q = B.th * m[N + 2] + B.vr * m[N];  // 2 <u^n v'^2 E'>
+    o[0] = ct * B.th * m[N];
+    o[1] = ct * B.th * m[N + 1];
+    const R diag = B.th * (c[0] * m[N] + c[1] * m[N + 1]) + R(0.5) * c[4] * q;
+    o[2] = T ? R(0) : diag;
+    o[3] = T ? diag : R(0);
+    o[4] = R(0.5) * ct * q;
 }
 
 template <typename R> struct Prim {
     R rho, U, V, W, lam, p;
+    R ir;  // 1/rho
+    R th;  // 1/(2 lam)
+    R q2;  // U^2 + (K+3)/(2 lam)
+    R c4;  // 4 lam^2/(K+3)
 };
 
-template <typename R> HK_HD Prim<R> primitive(const R Wc[5], R gamma, R Kp3)
+// iKp3 = 1/(K+3)
+template <typename R> HK_HD Prim<R> primitive(const R Wc[5], R gamma, R Kp3, R iKp3)
 {
     Prim<R> s;
     s.rho = Wc[0];
-    R ir = R(1) / Wc[0];
-    s.U = Wc[1] * ir;
-    s.V = Wc[2] * ir;
-    s.W = Wc[3] * ir;
+    s.ir = R(1) / Wc[0];
+    s.U = Wc[1] * s.ir;
+    s.V = Wc[2] * s.ir;
+    s.W = Wc[3] * s.ir;
     R eint = Wc[4] - R(0.5) * (Wc[1] * s.U + Wc[2] * s.V + Wc[3] * s.W);
     s.p = (gamma - R(1)) * eint;
     // rho E = rho |U|^2/2 + (K+3) rho/(4 lam)
     s.lam = Kp3 * Wc[0] / (R(4) * eint);
+    s.th = R(2) * iKp3 * eint * s.ir;
+    s.q2 = s.U * s.U + Kp3 * s.th;
+    s.c4 = R(4) * s.lam * s.lam * iKp3;
     return s;
 }
 
-template <typename R> HK_HD void full_moments(const Prim<R> &s, R K, Mom<R> &m)
+// Solve <(a . psi') psi'> = b for a Maxwellian with velocity (U, 0, 0) and
+// lam (the closed form in peculiar velocity, tangential velocities zero).
+template <typename R> HK_HD void micro_slope_u(const Prim<R> &s, const R b[5], R a[5])
 {
-    R th = R(0.5) / s.lam;
-    mom_full_1d(s.U, th, m.u);
-    mom_full_1d(s.V, th, m.v);
-    mom_full_1d(s.W, th, m.w);
-    m.xi2 = K * th;
-    m.xi4 = K * (K + R(2)) * th * th;
+    const R r1 = b[1] - s.U * b[0];
+    a[4] = s.c4 * (R(2) * b[4] - s.q2 * b[0] - R(2) * s.U * r1);
+    a[1] = R(2) * s.lam * r1 - s.U * a[4];
+    a[2] = R(2) * s.lam * b[2];
+    a[3] = R(2) * s.lam * b[3];
+    a[0] = b[0] - s.U * a[1] - R(0.5) * a[4] * s.q2;
+}
+
+// out += dF_i, the derivative of the Euler flux in direction i for the
+// derivative d of the conservative variables.  For a Maxwellian g_W and the
+// slope a with (a . psi) g = dg/dx_i this equals <u_i (a . psi) psi g>, the
+// moment the compatibility condition needs, in closed form.
+template <int I, typename R>
+HK_HD void euler_dflux(const Prim<R> &s, const R Wc[5], R ir, R gm1, const R d[5], R out[5])
+{
+    const R u[3] = {s.U, s.V, s.W};
+    R du[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) du[j] = (d[1 + j] - u[j] * d[0]) * ir;
+    const R dp = gm1 * (d[4] - (s.U * d[1] + s.V * d[2] + s.W * d[3]) + R(0.5) * (s.U * s.U + s.V * s.V + s.W * s.W) * d[0]);
+    out[0] += d[1 + I];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) out[1 + j] += d[1 + I] * u[j] + Wc[1 + I] * du[j];
+    out[1 + I] += dp;
+    out[4] += du[I] * (Wc[4] + s.p) + u[I] * (d[4] + dp);
 }
 
 // ---------------------------------------------------------------------------
@@ -226,12 +265,18 @@ template <typename R> HK_HD void full_moments(const Prim<R> &s, R K, Mom<R> &m)
 // u < 0 in eq. (flux), as in the half-space split of Q0.  Returns the flux
 // per unit area F^n and its time derivative, found from the time integrals
 // over dt and dt/2 (eq. expansion-1) in closed form.
+//
+// Every velocity moment of a Maxwellian is taken in the frame moving with
+// its tangential velocity (BMom), and the compatibility condition's
+// right-hand sides sum_i <u_i (a_i . psi) psi> are the Euler flux
+// derivatives (euler_dflux); both are exact rewritings of the moments.
 // ---------------------------------------------------------------------------
 template <typename R>
 HK_HD void gks_flux(const R Wl[5], const R dWl[3][5], const R Wr[5], const R dWr[3][5],
                                          const Scheme &S, R dt, R F[5], R dF[5])
 {
-    const R gamma = R(S.gamma), K = R(S.K), Kp3 = R(S.K) + R(3);
+    const R gamma = R(S.gamma), K = R(S.K), Kp3 = R(S.K) + R(3), gm1 = R(S.gamma) - R(1);
+    const R iKp3 = R(1.0 / (S.K + 3.0));
     const bool prfix = (S.mu > 0.0) && (S.Pr != 1.0);
 
     R W0[5], dW0[3][5], Fa[5], Fb[5], Fc[5], Sa[5], Sb[5], Sc[5];
@@ -246,65 +291,91 @@ HK_HD void gks_flux(const R Wl[5], const R dWl[3][5], const R Wr[5], const R dWr
     for (int side = 0; side < 2; ++side) {
         const R *Wc = side ? Wr : Wl;
         const R(*dW)[5] = side ? dWr : dWl;
-        Prim<R> s = primitive(Wc, gamma, Kp3);
+        const Prim<R> s = primitive(Wc, gamma, Kp3, iKp3);
         pside[side] = s.p;
-        R ir = R(1) / s.rho;
-        // spatial slopes a_i = M^{-1} dW/dn_i
-        R a[3][5];
+        const R ir = s.ir;
+        // time slope data: b_A = -(1/rho) sum_i dF_i
+        R bA[5] = {R(0), R(0), R(0), R(0), R(0)};
+        euler_dflux<0>(s, Wc, ir, gm1, dW[0], bA);
+        euler_dflux<1>(s, Wc, ir, gm1, dW[1], bA);
+        euler_dflux<2>(s, Wc, ir, gm1, dW[2], bA);
+        // spatial and time slopes in the tangentially moving frame
+        R a[3][5], A[5];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             R b[5];
 #pragma unroll
             for (int k = 0; k < 5; ++k) b[k] = dW[i][k] * ir;
-            micro_slope(s.U, s.V, s.W, s.lam, Kp3, b, a[i]);
+            boost_in(s.V, s.W, b);
+            micro_slope_u(s, b, a[i]);
         }
-        // time slope: <a_1 u + a_2 v + a_3 w + A> = 0
-        Mom<R> m;
-        full_moments(s, K, m);
-        R A[5];
-        {
-            R t1[5], t2[5], t3[5], b[5];
-            apsi_m<1, 0, 0>(m, a[0], t1);
-            apsi_m<0, 1, 0>(m, a[1], t2);
-            apsi_m<0, 0, 1>(m, a[2], t3);
 #pragma unroll
-            for (int k = 0; k < 5; ++k) b[k] = -(t1[k] + t2[k] + t3[k]);
-            micro_slope(s.U, s.V, s.W, s.lam, Kp3, b, A);
-        }
-        // switch u to the half line of this side
-        mom_half_1d(s.U, s.lam, R(0.5) / s.lam, side ? R(-1) : R(1), m.u);
+        for (int k = 0; k < 5; ++k) bA[k] = -bA[k] * ir;
+        boost_in(s.V, s.W, bA);
+        micro_slope_u(s, bA, A);
+        // u on the half line of this side
+        BMom<R> B;
+        mom_half_1d(s.U, s.lam, s.th, side ? R(-1) : R(1), B.m);
+        bmom_tangential(B, s.th, K);
         R t[5];
-        psi_m<0, 0, 0>(m, t);
+        bpsi<0>(B, t);
+        boost_out(s.V, s.W, t);
 #pragma unroll
         for (int k = 0; k < 5; ++k) W0[k] += s.rho * t[k];
+        R d1[5], d2[5];  // <(a_1 . psi') psi'>, <(a_2 . psi') psi'> (also used by Sb)
+        bapsi<0>(B, a[1], d1);
+        bapsi<0>(B, a[2], d2);
+        bapsi<0>(B, a[0], t);
+        boost_out(s.V, s.W, t);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            apsi_m<0, 0, 0>(m, a[i], t);
-#pragma unroll
-            for (int k = 0; k < 5; ++k) dW0[i][k] += s.rho * t[k];
+        for (int k = 0; k < 5; ++k) {
+            dW0[0][k] += s.rho * t[k];
+            t[k] = d1[k];
         }
-        psi_m<1, 0, 0>(m, t);
+        boost_out(s.V, s.W, t);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            dW0[1][k] += s.rho * t[k];
+            t[k] = d2[k];
+        }
+        boost_out(s.V, s.W, t);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) dW0[2][k] += s.rho * t[k];
+        bpsi<1>(B, t);
+        boost_out(s.V, s.W, t);
 #pragma unroll
         for (int k = 0; k < 5; ++k) Fa[k] += s.rho * t[k];
         {
-            R t1[5], t2[5], t3[5];
-            apsi_m<2, 0, 0>(m, a[0], t1);
-            apsi_m<1, 1, 0>(m, a[1], t2);
-            apsi_m<1, 0, 1>(m, a[2], t3);
+            // <u (u a_0 + v a_1 + w a_2) . psi psi> with v = V + v', w = W + w'
+            R t0[5], t1[5], t2[5], tv[5], tw[5];
+            bapsi<2>(B, a[0], t0);
+            bapsi<1>(B, a[1], t1);
+            bapsi<1>(B, a[2], t2);
+            bapsi_t<1, 0>(B, a[1], tv);
+            bapsi_t<1, 1>(B, a[2], tw);
 #pragma unroll
-            for (int k = 0; k < 5; ++k) Fb[k] += s.rho * (t1[k] + t2[k] + t3[k]);
+            for (int k = 0; k < 5; ++k) t[k] = t0[k] + s.V * t1[k] + tv[k] + s.W * t2[k] + tw[k];
+            boost_out(s.V, s.W, t);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) Fb[k] += s.rho * t[k];
         }
-        apsi_m<1, 0, 0>(m, A, t);
+        bapsi<1>(B, A, t);
+        boost_out(s.V, s.W, t);
 #pragma unroll
         for (int k = 0; k < 5; ++k) Fc[k] += s.rho * t[k];
         if (prfix) {
-            R t1[5], t2[5], t3[5];
-            apsi_m<1, 0, 0>(m, a[0], t1);
-            apsi_m<0, 1, 0>(m, a[1], t2);
-            apsi_m<0, 0, 1>(m, a[2], t3);
+            // sum_i <u_i (a_i . psi) psi> and <(A . psi) psi> on this half line
+            R t0[5], tv[5], tw[5];
+            bapsi<1>(B, a[0], t0);
+            bapsi_t<0, 0>(B, a[1], tv);
+            bapsi_t<0, 1>(B, a[2], tw);
 #pragma unroll
-            for (int k = 0; k < 5; ++k) Sb[k] += s.rho * (t1[k] + t2[k] + t3[k]);
-            apsi_m<0, 0, 0>(m, A, t);
+            for (int k = 0; k < 5; ++k) t[k] = t0[k] + s.V * d1[k] + tv[k] + s.W * d2[k] + tw[k];
+            boost_out(s.V, s.W, t);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) Sb[k] += s.rho * t[k];
+            bapsi<0>(B, A, t);
+            boost_out(s.V, s.W, t);
 #pragma unroll
             for (int k = 0; k < 5; ++k) Sc[k] += s.rho * t[k];
         }
@@ -313,48 +384,57 @@ HK_HD void gks_flux(const R Wl[5], const R dWl[3][5], const R Wr[5], const R dWr
     for (int k = 0; k < 5; ++k) Sa[k] = W0[k];
 
     // equilibrium state at the interface and its slopes
-    Prim<R> s0 = primitive(W0, gamma, Kp3);
-    R ir0 = R(1) / s0.rho;
-    R abar[3][5], Abar[5];
+    const Prim<R> s0 = primitive(W0, gamma, Kp3, iKp3);
+    const R ir0 = s0.ir;
+    R abar[3][5], Abar[5], S0b[5] = {R(0), R(0), R(0), R(0), R(0)};
+    euler_dflux<0>(s0, W0, ir0, gm1, dW0[0], S0b);
+    euler_dflux<1>(s0, W0, ir0, gm1, dW0[1], S0b);
+    euler_dflux<2>(s0, W0, ir0, gm1, dW0[2], S0b);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         R b[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) b[k] = dW0[i][k] * ir0;
-        micro_slope(s0.U, s0.V, s0.W, s0.lam, Kp3, b, abar[i]);
+        boost_in(s0.V, s0.W, b);
+        micro_slope_u(s0, b, abar[i]);
     }
-    Mom<R> m0;
-    full_moments(s0, K, m0);
-    R S0b[5];
     {
-        R t1[5], t2[5], t3[5], b[5];
-        apsi_m<1, 0, 0>(m0, abar[0], t1);
-        apsi_m<0, 1, 0>(m0, abar[1], t2);
-        apsi_m<0, 0, 1>(m0, abar[2], t3);
+        R b[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            S0b[k] = t1[k] + t2[k] + t3[k];
+            S0b[k] *= ir0;  // sum_i <u_i (abar_i . psi) psi> per unit density
             b[k] = -S0b[k];
         }
-        micro_slope(s0.U, s0.V, s0.W, s0.lam, Kp3, b, Abar);
+        boost_in(s0.V, s0.W, b);
+        micro_slope_u(s0, b, Abar);
+    }
+    BMom<R> B0;
+    {
+        mom_full_1d(s0.U, s0.th, B0.m);
+        bmom_tangential(B0, s0.th, K);
     }
     R F0a[5], F0b[5], F0c[5];
-    psi_m<1, 0, 0>(m0, F0a);
+    bpsi<1>(B0, F0a);
+    boost_out(s0.V, s0.W, F0a);
     {
-        R t1[5], t2[5], t3[5];
-        apsi_m<2, 0, 0>(m0, abar[0], t1);
-        apsi_m<1, 1, 0>(m0, abar[1], t2);
-        apsi_m<1, 0, 1>(m0, abar[2], t3);
+        R t0[5], t1[5], t2[5], tv[5], tw[5];
+        bapsi<2>(B0, abar[0], t0);
+        bapsi<1>(B0, abar[1], t1);
+        bapsi<1>(B0, abar[2], t2);
+        bapsi_t<1, 0>(B0, abar[1], tv);
+        bapsi_t<1, 1>(B0, abar[2], tw);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) F0b[k] = t1[k] + t2[k] + t3[k];
+        for (int k = 0; k < 5; ++k) F0b[k] = t0[k] + s0.V * t1[k] + tv[k] + s0.W * t2[k] + tw[k];
+        boost_out(s0.V, s0.W, F0b);
     }
-    apsi_m<1, 0, 0>(m0, Abar, F0c);
+    bapsi<1>(B0, Abar, F0c);
+    boost_out(s0.V, s0.W, F0c);
 
     // collision time (Sec. 4)
     R jump = m_abs((pside[0] - pside[1]) / (pside[0] + pside[1]));
     R tau;
     if (S.mu > 0.0)
-        tau = R(S.mu) / s0.p + R(S.tau_C) * jump * dt;
+        tau = R(S.mu) * R(2) * s0.lam * s0.ir + R(S.tau_C) * jump * dt;  // mu/p0, p0 = rho0/(2 lam0)
     else
         tau = (R(S.tau_eps) + R(S.tau_C) * jump) * dt;
 
@@ -362,17 +442,18 @@ HK_HD void gks_flux(const R Wl[5], const R dWl[3][5], const R Wr[5], const R dWr
     // Fh(delta) = sum_j q_j(delta) M_j, with q_j the time integrals of the
     // factors of eq. (flux); the combinations c_j, d_j below are those
     // integrals worked out with e2 = exp(-dt/(2 tau)), e1 = e2^2.
-    R x = dt / (R(2) * tau);
+    const R idt = R(1) / dt;
+    R x = R(0.5) * dt / tau;
     R om = -m_expm1(-x);  // 1 - e2
     R e2 = R(1) - om;
     R e1 = e2 * e2;
-    R r = tau / dt;
+    R r = tau * idt;
     R E3 = om * (R(3) - e2);
     R Dq = om * om;
     R c3 = r * E3, c0 = R(1) - c3, c2 = -tau * c0, c5 = -tau * c3;
     R c1 = tau * (e1 - R(2) * e2 - R(1)) + R(2) * tau * r * E3;
     R c4 = -tau - c1;
-    R d0 = R(4) * r * Dq / dt, d3 = -d0, d2 = R(1) - tau * d0, d5 = tau * d0;
+    R d0 = R(4) * r * Dq * idt, d3 = -d0, d2 = R(1) - tau * d0, d5 = tau * d0;
     R d1 = R(4) * r * (e2 - e1) - R(8) * r * r * Dq, d4 = -d1;
 
 #pragma unroll

@@ -9,7 +9,7 @@
 #include "hgks_device.cuh"
 
 struct Counts {
-    long add = 0, mul = 0, div = 0, sqrt = 0, exp = 0, expm1 = 0, erfc = 0;
+    long add = 0, mul = 0, div = 0, sqrt = 0, rsqrt = 0, exp = 0, expm1 = 0, erfc = 0;
     void reset() { *this = Counts(); }
 };
 static Counts C;
@@ -33,15 +33,16 @@ inline CR m_exp(CR a) { ++C.exp; return CR(std::exp(a.v)); }
 inline CR m_expm1(CR a) { ++C.expm1; return CR(std::expm1(a.v)); }
 inline CR m_erfc(CR a) { ++C.erfc; return CR(std::erfc(a.v)); }
 inline CR m_sqrt(CR a) { ++C.sqrt; return CR(std::sqrt(a.v)); }
+inline CR m_rsqrt(CR a) { ++C.rsqrt; return CR(1.0 / std::sqrt(a.v)); }
 inline CR m_abs(CR a) { return CR(std::fabs(a.v)); }
 inline CR m_max(CR a, CR b) { return CR(a.v > b.v ? a.v : b.v); }
 
 static void print(const char *name, long scale_num = 1)
 {
     long fl = C.add + C.mul;
-    printf("  \"%s\": {\"add\": %ld, \"mul\": %ld, \"div\": %ld, \"sqrt\": %ld, \"exp\": %ld, \"expm1\": %ld, "
-           "\"erfc\": %ld, \"addmul\": %ld}",
-           name, C.add, C.mul, C.div, C.sqrt, C.exp, C.expm1, C.erfc, fl);
+    printf("  \"%s\": {\"add\": %ld, \"mul\": %ld, \"div\": %ld, \"sqrt\": %ld, \"rsqrt\": %ld, \"exp\": %ld, "
+           "\"expm1\": %ld, \"erfc\": %ld, \"addmul\": %ld}",
+           name, C.add, C.mul, C.div, C.sqrt, C.rsqrt, C.exp, C.expm1, C.erfc, fl);
     (void)scale_num;
 }
 
