@@ -220,6 +220,7 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
     S.Gamma_lin = 0.0025;
     S.weno_pow = 1;
     S.limiter = 1;
+    hk::scheme_derive(S);
     h->precision = grid->precision;
 
     if (stream) {
@@ -329,6 +330,7 @@ extern "C" int hgks_set_option(hgks_t *h, const char *key, double value)
     } else {
         return fail(h, HGKS_E_INVALID, "unknown option %s", key);
     }
+    hk::scheme_derive(h->S);
     return HGKS_OK;
 }
 
@@ -601,6 +603,7 @@ extern "C" int hgks_point_flux(int n, const double *in, const double *ug, double
     S.Gamma_lin = 0.0025;
     S.weno_pow = 1;
     S.limiter = 1;
+    hk::scheme_derive(S);
     double *buf = nullptr;
     size_t nin = (size_t)n * 40, nug = ug ? (size_t)n * 3 : 0, nout = (size_t)n * 10;
     if (cudaMalloc((void **)&buf, (nin + nug + nout) * sizeof(double)) != cudaSuccess) {

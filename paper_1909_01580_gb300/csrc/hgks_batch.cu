@@ -544,6 +544,7 @@ extern "C" int hgks_batch_add(hgks_batch_t *b, const hgks_grid_t *grid, double g
     S.Gamma_lin = 0.0025;
     S.weno_pow = 1;
     S.limiter = 1;
+    hk::scheme_derive(S);
     unsigned char *p = b->arena + off;
     in.Qn = (double *)p;
     p += sz[0];

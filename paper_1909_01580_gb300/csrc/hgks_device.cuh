@@ -38,7 +38,17 @@ HK_HD double m_max(double a, double b) { return fmax(a, b); }
 HK_HD float m_max(float a, float b) { return fmaxf(a, b); }
 HK_HD float m_abs(float x) { return fabsf(x); }
 
-// Scheme constants, passed by value to every kernel.
+// Constants of the Gauss-point flux in one working precision, derived on the
+// host (scheme_derive) so that no thread converts or divides them.
+template <typename R> struct FluxK {
+    R gamma, K, Kp3, iKp3, gm1;  // gamma, K, K + 3, 1/(K + 3), gamma - 1
+    R mu2;                       // 2 mu
+    R tau_eps, tau_C;
+    R prfac;                     // 1/Pr - 1
+};
+
+// Scheme constants, passed by value to every kernel.  After any change of
+// the fields above kd/kf, scheme_derive() must be called.
 struct Scheme {
     double gamma;      // ratio of specific heats
     double K;          // internal degrees of freedom (5 - 3 gamma)/(gamma - 1)
@@ -48,7 +58,43 @@ struct Scheme {
     double Gamma_lin;  // linear weight of each sub-stencil
     int weno_pow;      // exponent on tau/(beta + eps)
     int limiter;       // positivity fallback on/off
+    int viscous;       // mu > 0
+    int prfix;         // mu > 0 and Pr != 1: Prandtl correction of the energy flux
+    FluxK<double> kd;
+    FluxK<float> kf;
 };
+
+template <typename R> HK_HD void fluxk_fill(const Scheme &S, FluxK<R> &k)
+{
+    k.gamma = R(S.gamma);
+    k.K = R(S.K);
+    k.Kp3 = R(S.K + 3.0);
+    k.iKp3 = R(1.0 / (S.K + 3.0));
+    k.gm1 = R(S.gamma - 1.0);
+    k.mu2 = R(2.0 * S.mu);
+    k.tau_eps = R(S.tau_eps);
+    k.tau_C = R(S.tau_C);
+    k.prfac = R(1.0 / S.Pr - 1.0);
+}
+
+inline void scheme_derive(Scheme &S)
+{
+    S.viscous = S.mu > 0.0;
+    S.prfix = S.mu > 0.0 && S.Pr != 1.0;
+    fluxk_fill(S, S.kd);
+    fluxk_fill(S, S.kf);
+}
+
+// the constants in precision R: stored for double and float, converted for
+// any other scalar (the host operation counter)
+template <typename R> HK_HD FluxK<R> fluxk(const Scheme &S)
+{
+    FluxK<R> k;
+    fluxk_fill(S, k);
+    return k;
+}
+template <> HK_HD FluxK<double> fluxk<double>(const Scheme &S) { return S.kd; }
+template <> HK_HD FluxK<float> fluxk<float>(const Scheme &S) { return S.kf; }
 
 // Mesh: a uniform grid of cubes with GH = 2 ghost layers in the state
 // arrays and one ghost layer in the reconstruction arrays.
@@ -275,9 +321,9 @@ template <typename R>
 HK_HD void gks_flux(const R Wl[5], const R dWl[3][5], const R Wr[5], const R dWr[3][5],
                                          const Scheme &S, R dt, R F[5], R dF[5])
 {
-    const R gamma = R(S.gamma), K = R(S.K), Kp3 = R(S.K) + R(3), gm1 = R(S.gamma) - R(1);
-    const R iKp3 = R(1.0 / (S.K + 3.0));
-    const bool prfix = (S.mu > 0.0) && (S.Pr != 1.0);
+    const FluxK<R> C = fluxk<R>(S);
+    const R gamma = C.gamma, K = C.K, Kp3 = C.Kp3, gm1 = C.gm1, iKp3 = C.iKp3;
+    const bool prfix = S.prfix != 0;
 
     R W0[5], dW0[3][5], Fa[5], Fb[5], Fc[5], Sa[5], Sb[5], Sc[5];
 #pragma unroll
@@ -433,10 +479,10 @@ HK_HD void gks_flux(const R Wl[5], const R dWl[3][5], const R Wr[5], const R dWr
     // collision time (Sec. 4)
     R jump = m_abs((pside[0] - pside[1]) / (pside[0] + pside[1]));
     R tau;
-    if (S.mu > 0.0)
-        tau = R(S.mu) * R(2) * s0.lam * s0.ir + R(S.tau_C) * jump * dt;  // mu/p0, p0 = rho0/(2 lam0)
+    if (S.viscous)
+        tau = C.mu2 * s0.lam * s0.ir + C.tau_C * jump * dt;  // mu/p0, p0 = rho0/(2 lam0)
     else
-        tau = (R(S.tau_eps) + R(S.tau_C) * jump) * dt;
+        tau = (C.tau_eps + C.tau_C * jump) * dt;
 
     // F = (4 Fh(dt/2) - Fh(dt))/dt and dF = 4 (Fh(dt) - 2 Fh(dt/2))/dt^2 for
     // Fh(delta) = sum_j q_j(delta) M_j, with q_j the time integrals of the
@@ -479,7 +525,7 @@ HK_HD void gks_flux(const R Wl[5], const R dWl[3][5], const R Wr[5], const R dWr
                - s0.U * (Sx[4] - (s0.U * Sx[1] + s0.V * Sx[2] + s0.W * Sx[3]) + uu * Sx[0]);
         R qd = dF[4] - (s0.U * dF[1] + s0.V * dF[2] + s0.W * dF[3]) + uu * dF[0]
                - s0.U * (Sd[4] - (s0.U * Sd[1] + s0.V * Sd[2] + s0.W * Sd[3]) + uu * Sd[0]);
-        R fac = R(1) / R(S.Pr) - R(1);
+        const R fac = C.prfac;
         F[4] += fac * qf;
         dF[4] += fac * qd;
     }

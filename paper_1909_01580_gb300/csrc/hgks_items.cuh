@@ -139,7 +139,8 @@ __device__ __forceinline__ void recon_item(const double *__restrict__ Q, R *__re
     // positivity fallback: the cheap sufficient test first, the literal
     // check of all 25 polynomials at the 24 Gauss points only when it fails
     bool bad = false;
-    if (S.limiter && !positivity_certain(qcv, rad, R(S.gamma))) bad = positivity_violated<R>(Q, g, i, j, k, R(S.gamma));
+    if (S.limiter && !positivity_certain(qcv, rad, fluxk<R>(S).gamma))
+        bad = positivity_violated<R>(Q, g, i, j, k, fluxk<R>(S).gamma);
     if (bad) {
         for (int v = 0; v < 5; ++v)
             for (int n = 1; n < 10; ++n) coef[coef_slot(v, n) * g.cstride + t] = R(0);
@@ -160,10 +161,13 @@ template <typename R, int D>
 __device__ __forceinline__ void eval_side(const R *__restrict__ coef, const Geo &g, long long ci, R xd, R xa, R xb,
                                           R W[5], R dW[3][5])
 {
-    R X[3];
-    X[D] = xd;
-    X[(D + 1) % 3] = xa;
-    X[(D + 2) % 3] = xb;
+    // at a face Gauss point the face-normal coordinate is xd = +-1/2 and the
+    // tangential ones are +-1/(2 sqrt 3), so the zero-mean tangential squares
+    // X_A^2 - 1/12 and X_B^2 - 1/12 vanish and X_D^2 - 1/12 = 1/6
+    constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
+    constexpr int DA = D + A == 1 ? 6 : (D + A == 2 ? 7 : 8);
+    constexpr int DB = D + B == 1 ? 6 : (D + B == 2 ? 7 : 8);
+    constexpr int AB = A + B == 1 ? 6 : (A + B == 2 ? 7 : 8);
     const R ih = R(g.inv_h);
     R val[5], grad[5][3];
 #pragma unroll
@@ -171,9 +175,11 @@ __device__ __forceinline__ void eval_side(const R *__restrict__ coef, const Geo 
         R c[9];
 #pragma unroll
         for (int n = 0; n < 9; ++n) c[n] = coef[coef_slot(v, 1 + n) * g.cstride + ci];
-        R s;
-        poly_value_grad(c, X, ih, s, grad[v]);
-        val[v] = coef[coef_slot(v, 0) * g.cstride + ci] + s;
+        val[v] = coef[coef_slot(v, 0) * g.cstride + ci] + (c[D] * xd + c[3 + D] * R(1.0 / 6.0)) +
+                 xa * (c[A] + c[DA] * xd) + xb * (c[B] + c[DB] * xd) + c[AB] * xa * xb;
+        grad[v][D] = (c[D] + R(2) * c[3 + D] * xd + c[DA] * xa + c[DB] * xb) * ih;
+        grad[v][A] = (c[A] + R(2) * c[3 + A] * xa + c[DA] * xd + c[AB] * xb) * ih;
+        grad[v][B] = (c[B] + R(2) * c[3 + B] * xb + c[DB] * xd + c[AB] * xa) * ih;
     }
     // local frame: local axis l is global axis (D + l) % 3
     W[0] = val[0];

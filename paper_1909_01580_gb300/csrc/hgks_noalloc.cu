@@ -130,6 +130,7 @@ extern "C" int hgks_flux_noalloc(const hgks_grid_t *grid, double gamma, double m
     S.Gamma_lin = 0.0025;
     S.weno_pow = 1;
     S.limiter = 1;
+    hk::scheme_derive(S);
 
     // carve the scratch: control block, padded state, coefficients, flags,
     // face fluxes of the three axes

@@ -51,6 +51,7 @@ int main()
     hk::Scheme S;
     S.gamma = 1.4; S.K = 2.0; S.mu = 0.0; S.Pr = 1.0; S.tau_eps = 0.01; S.tau_C = 1.0;
     S.weno_eps = 1e-8; S.Gamma_lin = 0.0025; S.weno_pow = 1; S.limiter = 1;
+    hk::scheme_derive(S);
     printf("{\n");
     // reconstruction of one cell: 5 variables and the positivity test
     C.reset();
@@ -71,6 +72,7 @@ int main()
     for (int viscous = 0; viscous < 2; ++viscous) {
         S.mu = viscous ? 1e-3 : 0.0;
         S.Pr = viscous ? 0.72 : 1.0;
+        hk::scheme_derive(S);
         C.reset();
         CR X[3] = {0.5, 0.288, -0.288}, ih = 16.0;
         CR W[2][5], dW[2][3][5];
