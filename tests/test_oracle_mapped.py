@@ -122,3 +122,17 @@ def test_free_stream_table4_map_16():
     l1 = float(np.abs(q1[0] - q[0]).reshape(-1) @ vol)
     print(f"Table 4, 16^3: oracle L1 = {l1:.3e} (paper {rows[0, 1]:.3e})")
     assert l1 < 10 * rows[0, 1]
+
+
+def test_mapped_initial_averages():
+    """The Table 2 initial data on trilinear cells: with amplitude 0 they are
+    the exact uniform averages (to the quadrature's error), and the
+    volume-weighted sum is the integral of rho over the box (8, the sine
+    integrates to zero over its periods)."""
+    n = (8, 8, 8)
+    q0 = W.density_advection_mapped(n, amp=0.0)
+    assert np.abs(q0 - W.density_advection(n)).max() < 1e-9
+    q = W.density_advection_mapped(n, amp=0.1)
+    vol = oracle.volumes(oracle.make_cfg(n, mesh=1, amp=0.1, omega=0.0), 0.0)
+    assert abs(float((q[0] * vol).sum()) - 8.0) < 1e-12
+    assert abs(float(vol.sum()) - 8.0) < 1e-12
