@@ -51,7 +51,7 @@ enum { HGKS_FP64 = 0,   /* every operation in FP64                              
                            accumulation and the two-stage update in FP64         */
 };
 
-enum { HGKS_BC_PERIODIC = 0, HGKS_BC_REFLECTIVE = 1 };
+enum { HGKS_BC_PERIODIC = 0, HGKS_BC_REFLECTIVE = 1, HGKS_BC_OUTFLOW = 2 };
 
 enum {
     HGKS_OK = 0,
@@ -74,8 +74,11 @@ enum {
  *   Pr      Prandtl number; when mu > 0 and Pr != 1 the energy flux takes the
  *           heat-flux correction F_E += (1/Pr - 1) q (the paper is silent on
  *           Pr; this is the usual BGK correction).
- *   bc      per face -x,+x,-y,+y,-z,+z: HGKS_BC_PERIODIC (must pair) or
- *           HGKS_BC_REFLECTIVE (mirror, normal momentum negated).
+ *   bc      per face -x,+x,-y,+y,-z,+z: HGKS_BC_PERIODIC (must pair),
+ *           HGKS_BC_REFLECTIVE (mirror, normal momentum negated) or
+ *           HGKS_BC_OUTFLOW (the non-reflecting boundary of the Riemann
+ *           problems of Sec. 4, read as zero-gradient extrapolation: every
+ *           ghost layer repeats the boundary cell).
  *   stream  cudaStream_t to order all work on, or NULL for a private stream.
  *   out     receives the handle.
  * Paper constants are defaults: Gamma = 0.0025 (gamma_0 = 0.94), epsilon

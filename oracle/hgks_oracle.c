@@ -45,7 +45,8 @@ typedef struct {
     double amp;        /* mapped mesh: x_d = xi_d + amp*S(t)*prod sin(...)   */
     double omega;      /* moving mesh: S(t) = sin(omega t); static: S = 1    */
     double gamma, mu, Pr;
-    int bc[6];         /* -x,+x,-y,+y,-z,+z : 0 periodic, 1 reflective       */
+    int bc[6];         /* -x,+x,-y,+y,-z,+z : 0 periodic, 1 reflective,
+                          2 non-reflecting (outflow)                          */
     double Gamma_lin;  /* linear weight of each sub-stencil (Sec. 2)         */
     double weno_eps;   /* epsilon of the nonlinear weights                   */
     int weno_pow;      /* exponent on tau/(beta+eps); 1 as printed           */
@@ -319,9 +320,12 @@ static void geom_free(orc_geom *G)
 
 /* Copy the interior state into the padded array and fill GH ghost layers.
  * Periodic boundaries wrap; reflective ("symmetric") boundaries mirror the
- * cell order and negate the momentum normal to that boundary.  Edge and
- * corner ghosts take every applicable wrap or mirror, since the big
- * stencil reaches the edge neighbours. */
+ * cell order and negate the momentum normal to that boundary; non-reflecting
+ * (outflow) boundaries repeat the boundary cell in every ghost layer
+ * (zero-gradient extrapolation, the reading of the non-reflecting condition
+ * of the Riemann problems of Sec. 4).  Edge and corner ghosts take every
+ * applicable wrap, mirror or repeat, since the big stencil reaches the edge
+ * neighbours. */
 static void fill_ghosts(const orc_cfg *c, const orc_dims *D, const double *q, double *Qp)
 {
     size_t ncint = (size_t)c->n[0] * c->n[1] * c->n[2];
@@ -332,9 +336,13 @@ static void fill_ghosts(const orc_cfg *c, const orc_dims *D, const double *q, do
                 for (int d = 0; d < 3; ++d) {
                     int n = c->n[d], s = idx[d];
                     if (s < 0) {
-                        if (c->bc[2 * d] == 0) s += n; else { s = -1 - s; flip[d] = 1; }
+                        if (c->bc[2 * d] == 0) s += n;
+                        else if (c->bc[2 * d] == 2) s = 0;
+                        else { s = -1 - s; flip[d] = 1; }
                     } else if (s >= n) {
-                        if (c->bc[2 * d + 1] == 0) s -= n; else { s = 2 * n - 1 - s; flip[d] = 1; }
+                        if (c->bc[2 * d + 1] == 0) s -= n;
+                        else if (c->bc[2 * d + 1] == 2) s = n - 1;
+                        else { s = 2 * n - 1 - s; flip[d] = 1; }
                     }
                     src[d] = s;
                 }

@@ -181,7 +181,8 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
         if ((bc[2 * d] == HGKS_BC_PERIODIC) != (bc[2 * d + 1] == HGKS_BC_PERIODIC))
             return fail(nullptr, HGKS_E_INVALID, "periodic boundaries must pair%s");
         for (int s = 0; s < 2; ++s)
-            if (bc[2 * d + s] != HGKS_BC_PERIODIC && bc[2 * d + s] != HGKS_BC_REFLECTIVE)
+            if (bc[2 * d + s] != HGKS_BC_PERIODIC && bc[2 * d + s] != HGKS_BC_REFLECTIVE &&
+                bc[2 * d + s] != HGKS_BC_OUTFLOW)
                 return fail(nullptr, HGKS_E_INVALID, "unknown boundary condition%s");
     }
     int ndev = 0;

@@ -231,7 +231,8 @@ static int validate_grid(const hgks_grid_t *grid, double gamma, double mu, doubl
     for (int d = 0; d < 3; ++d) {
         if ((bc[2 * d] == HGKS_BC_PERIODIC) != (bc[2 * d + 1] == HGKS_BC_PERIODIC)) return HGKS_E_INVALID;
         for (int s = 0; s < 2; ++s)
-            if (bc[2 * d + s] != HGKS_BC_PERIODIC && bc[2 * d + s] != HGKS_BC_REFLECTIVE) return HGKS_E_INVALID;
+            if (bc[2 * d + s] != HGKS_BC_PERIODIC && bc[2 * d + s] != HGKS_BC_REFLECTIVE &&
+                bc[2 * d + s] != HGKS_BC_OUTFLOW) return HGKS_E_INVALID;
     }
     *hx_out = hx;
     return HGKS_OK;

@@ -13,9 +13,10 @@ namespace hk {
 #define GAUSS_S 0.28867513459481288225
 
 // ---------------------------------------------------------------------------
-// ghost cells: periodic wrap or reflective mirror (normal momentum negated),
-// width 2 including edge and corner ghosts; every ghost reads its interior
-// source directly, so one pass fills all of them.  t: padded linear index.
+// ghost cells: periodic wrap, reflective mirror (normal momentum negated) or
+// non-reflecting outflow (the boundary cell repeated), width 2 including
+// edge and corner ghosts; every ghost reads its interior source directly, so
+// one pass fills all of them.  t: padded linear index.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void halo_item(double *__restrict__ Q, const Geo &g, long long t)
 {
@@ -32,10 +33,12 @@ __device__ __forceinline__ void halo_item(double *__restrict__ Q, const Geo &g, 
         if (s < 0) {
             ghost = true;
             if (g.bc[2 * d] == 0) s += n[d];
+            else if (g.bc[2 * d] == 2) s = 0;
             else { s = -1 - s; flip[d] = 1; }
         } else if (s >= n[d]) {
             ghost = true;
             if (g.bc[2 * d + 1] == 0) s -= n[d];
+            else if (g.bc[2 * d + 1] == 2) s = n[d] - 1;
             else { s = 2 * n[d] - 1 - s; flip[d] = 1; }
         }
         src[d] = s;

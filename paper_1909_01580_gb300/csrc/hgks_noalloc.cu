@@ -80,7 +80,8 @@ extern "C" int hgks_flux_noalloc(const hgks_grid_t *grid, double gamma, double m
             return HGKS_E_INVALID;
         }
         for (int s = 0; s < 2; ++s)
-            if (bc[2 * d + s] != HGKS_BC_PERIODIC && bc[2 * d + s] != HGKS_BC_REFLECTIVE) {
+            if (bc[2 * d + s] != HGKS_BC_PERIODIC && bc[2 * d + s] != HGKS_BC_REFLECTIVE &&
+                bc[2 * d + s] != HGKS_BC_OUTFLOW) {
                 hgks_internal_set_error("hgks_flux_noalloc: unknown boundary condition");
                 return HGKS_E_INVALID;
             }

@@ -18,6 +18,7 @@ HGKS_FP64 = 0
 HGKS_MIXED = 1
 HGKS_BC_PERIODIC = 0
 HGKS_BC_REFLECTIVE = 1
+HGKS_BC_OUTFLOW = 2
 HGKS_OK = 0
 HGKS_E_INVALID = -1
 HGKS_E_NOMEM = -2

@@ -128,6 +128,44 @@ def density_advection_mapped(n, amp=0.1, t=0.0, gamma=1.4, lo=(0.0, 0.0, 0.0), h
     return _conservative(rho, one, one, one, one, gamma)
 
 
+def riemann_x(n, left, right, x0, lo=(0.0, 0.0, 0.0), hi=(1.0, 0.1, 0.1), gamma=1.4):
+    """A 1D Riemann problem along x in a 3D box: (rho, U, p) = left for
+    x < x0 and right for x > x0, V = W = 0.  Cell averages, exact when x0
+    falls on a cell face; a cell cut by x0 gets the volume-weighted mix."""
+    box = Box(tuple(n), tuple(lo), tuple(hi))
+    hx = box.h[0]
+    edges = lo[0] + np.arange(n[0] + 1) * hx
+    frac_left = np.clip((x0 - edges[:-1]) / hx, 0.0, 1.0)  # fraction of each cell left of x0
+    cons_l = np.array([left[0], left[0] * left[1], 0.0, 0.0, left[2] / (gamma - 1.0) + 0.5 * left[0] * left[1] ** 2])
+    cons_r = np.array([right[0], right[0] * right[1], 0.0, 0.0,
+                       right[2] / (gamma - 1.0) + 0.5 * right[0] * right[1] ** 2])
+    line = cons_l[:, None] * frac_left[None, :] + cons_r[:, None] * (1.0 - frac_left[None, :])
+    return np.ascontiguousarray(np.broadcast_to(line[:, None, None, :], (5, n[2], n[1], n[0])), dtype=np.float64)
+
+
+def sod(n, lo=(0.0, 0.0, 0.0), hi=(1.0, 0.1, 0.1), gamma=1.4):
+    """Sod problem of Sec. 4: (rho, U, p) = (1, 0, 1) for x < 0.5 and
+    (0.125, 0, 0.1) for x > 0.5 on [0,1] x [0,0.1] x [0,0.1]."""
+    return riemann_x(n, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 0.5, lo, hi, gamma)
+
+
+def blast_wave(n, lo=(0.0, 0.0, 0.0), hi=(100.0, 10.0, 10.0), gamma=1.4, p_mid=0.01):
+    """Woodward-Colella blast wave of Sec. 4 on [0,100] x [0,10] x [0,10]:
+    rho = 1, U = 0 and p = 1000 for x < 10, p_mid (0.01 in the paper) for
+    10 < x < 90, 100 for x > 90 (cell averages; the planes x = 10, 90 fall
+    on faces when the cell size divides 10)."""
+    box = Box(tuple(n), tuple(lo), tuple(hi))
+    hx = box.h[0]
+    edges = lo[0] + np.arange(n[0] + 1) * hx
+    f1 = np.clip((10.0 - edges[:-1]) / hx, 0.0, 1.0)
+    f3 = np.clip((edges[1:] - 90.0) / hx, 0.0, 1.0)
+    p = 1000.0 * f1 + 100.0 * f3 + p_mid * (1.0 - f1 - f3)
+    line = np.zeros((5, n[0]))
+    line[0] = 1.0
+    line[4] = p / (gamma - 1.0)
+    return np.ascontiguousarray(np.broadcast_to(line[:, None, None, :], (5, n[2], n[1], n[0])), dtype=np.float64)
+
+
 def taylor_green(n, mach=0.1, gamma=1.4, L=1.0, V0=1.0, rho0=1.0):
     """Taylor-Green vortex on [-pi L, pi L]^3 (Sec. 4): u = V0 sin x cos y cos z,
     v = -V0 cos x sin y cos z, w = 0, p = p0 + rho0 V0^2/16 (cos 2x + cos 2y)(cos 2z + 2).
