@@ -277,15 +277,23 @@ def serving_run(count=16, sizes=(24, 32, 48), steps=(20, 40), seed=0, load=1.25,
            "arrival_rate_per_s": rate, "load_vs_sequential_fp64": load, "arena_gb": arena_gb,
            "fifo_fp64": serving.summary("fifo_fp64", base, reqs)}
     cells = sum(2 * r.cells * r.steps_target for r in reqs)
+    # admission policies: every arrived request that fits (fifo), or the
+    # least work first with a cap on the resident cells (sjf; FP64 fills the
+    # GPU with one mid-size instance, the mixed path wants more per launch)
+    caps = {"fp64": 120_000, "mixed": 1_000_000}
     for name in precisions:
         prec = hgks.HGKS_FP64 if name == "fp64" else hgks.HGKS_MIXED
-        res = serving.serve_batched(reqs, precision=prec, arena_bytes=int(arena_gb * (1 << 30)),
-                                    max_instances=64, steps_per_poll=4, keep_results=False)
-        s = serving.summary(f"batched_{name}", res, reqs)
-        s["max_resident"] = res["max_resident"]
-        s["gpu_launches"] = res["launches"]
-        s["cell_stage_updates_per_s"] = res["cell_stages"] / res["makespan"]
-        out[f"batched_{name}"] = s
+        for policy in ("fifo", "sjf"):
+            res = serving.serve_batched(reqs, precision=prec, arena_bytes=int(arena_gb * (1 << 30)),
+                                        max_instances=64, steps_per_poll=4, keep_results=False, policy=policy,
+                                        max_resident_cells=caps[name] if policy == "sjf" else None)
+            key = f"batched_{name}" + ("_sjf" if policy == "sjf" else "")
+            s = serving.summary(key, res, reqs)
+            s["policy"] = policy if policy == "fifo" else f"sjf, resident cells <= {caps[name]}"
+            s["max_resident"] = res["max_resident"]
+            s["gpu_launches"] = res["launches"]
+            s["cell_stage_updates_per_s"] = res["cell_stages"] / res["makespan"]
+            out[key] = s
     out["approx_cell_stages"] = cells
     return out
 

@@ -137,12 +137,36 @@ def serve_fifo(reqs, precision=hgks.HGKS_FP64):
     return out
 
 
+def next_admission(waiting, resident_cells, policy="fifo", max_resident_cells=None):
+    """Index into `waiting` (requests that have arrived, in arrival order) of
+    the request to admit next, or None to wait.
+      policy "fifo": the oldest request;
+      policy "sjf":  the request with the least estimated work (cells x
+                     target steps), ties by arrival.
+    With max_resident_cells, a request is admitted only while the resident
+    cells stay within the cap (always when nothing is resident), so that
+    the batch holds enough work to fill the GPU without sharing it among
+    more requests than that needs."""
+    if not waiting:
+        return None
+    if policy == "fifo":
+        k = 0
+    elif policy == "sjf":
+        k = min(range(len(waiting)), key=lambda i: (waiting[i].cells * waiting[i].steps_target, i))
+    else:
+        raise ValueError(f"unknown policy {policy}")
+    if max_resident_cells is not None and resident_cells > 0 and \
+            resident_cells + waiting[k].cells > max_resident_cells:
+        return None
+    return k
+
+
 def serve_batched(reqs, precision=hgks.HGKS_FP64, arena_bytes=4 << 30, max_instances=64, steps_per_poll=4,
-                  tuning=None, cfl=0.35, keep_results=True):
+                  tuning=None, cfl=0.35, keep_results=True, policy="fifo", max_resident_cells=None):
     """Continuous batching in real time: arrivals are released at their
-    arrival times (relative to the start of the call), admitted in order
-    when the arena and a slot are free, advanced together by batch steps,
-    and read back when they reach their end time."""
+    arrival times (relative to the start of the call), admitted by
+    next_admission() when the arena and a slot are free, advanced together by
+    batch steps, and read back when they reach their end time."""
     b = hgks.Batch(precision, arena_bytes=arena_bytes, max_instances=max_instances)
     if tuning is not None:
         b.set_tuning(tuning)
@@ -153,24 +177,32 @@ def serve_batched(reqs, precision=hgks.HGKS_FP64, arena_bytes=4 << 30, max_insta
     max_resident = 0
     t_start = time.perf_counter()
     last_steps = {}
-    while pending or by_slot:
+    waiting = []
+    while pending or waiting or by_slot:
         now = time.perf_counter() - t_start
-        # admit in arrival order while the head fits
         while pending and pending[0].arrival <= now:
-            r = pending[0]
+            waiting.append(pending.pop(0))
+        # admit by the policy while the choice fits the arena
+        while waiting:
+            k = next_admission(waiting, sum(r.cells for r in by_slot.values()), policy, max_resident_cells)
+            if k is None:
+                break
+            r = waiting[k]
             try:
                 sl = b.add((r.n,) * 3, r.lo, r.hi, r.q0, t0=0.0, t_end=r.t_end, cfl=cfl, mu=r.mu, Pr=r.Pr)
             except hgks.HgksError as e:
                 if e.code == hgks.HGKS_E_NOMEM:
+                    if not by_slot:
+                        raise RuntimeError(f"request {r.rid} ({r.n}^3) does not fit the arena alone") from e
                     break  # wait for memory or a slot
                 raise
             by_slot[sl] = r
             admitted_at[r.rid] = now
             last_steps[sl] = 0
-            pending.pop(0)
+            waiting.pop(k)
         max_resident = max(max_resident, len(by_slot))
         if not by_slot:
-            if pending:
+            if pending and not waiting:
                 time.sleep(max(0.0, pending[0].arrival - (time.perf_counter() - t_start)))
             continue
         b.step(steps_per_poll)
