@@ -60,12 +60,13 @@ class Cfg(ctypes.Structure):
         ("tau_C", ctypes.c_double),
         ("limiter", ctypes.c_int),
         ("nthreads", ctypes.c_int),
+        ("charvar", ctypes.c_int),
     ]
 
 
 def make_cfg(n, lo=(0.0, 0.0, 0.0), hi=(2.0, 2.0, 2.0), *, gamma=1.4, mu=0.0, Pr=1.0,
              bc=(0, 0, 0, 0, 0, 0), mesh=0, amp=0.0, omega=0.0, Gamma_lin=0.0025,
-             weno_eps=1e-8, weno_pow=1, tau_eps=0.01, tau_C=1.0, limiter=1, nthreads=0) -> Cfg:
+             weno_eps=1e-8, weno_pow=1, tau_eps=0.01, tau_C=1.0, limiter=1, nthreads=0, charvar=0) -> Cfg:
     """Configuration with the paper's defaults (Gamma = 0.0025, tau constants
     eps = 0.01 and C = 1 of Sec. 4, gamma = 1.4)."""
     c = Cfg()
@@ -80,6 +81,7 @@ def make_cfg(n, lo=(0.0, 0.0, 0.0), hi=(2.0, 2.0, 2.0), *, gamma=1.4, mu=0.0, Pr
     c.Gamma_lin, c.weno_eps, c.weno_pow = float(Gamma_lin), float(weno_eps), int(weno_pow)
     c.tau_eps, c.tau_C = float(tau_eps), float(tau_C)
     c.limiter, c.nthreads = int(limiter), int(nthreads)
+    c.charvar = int(charvar)
     return c
 
 
@@ -116,6 +118,8 @@ def lib():
             L.orc_time_integrals.argtypes = [D, D, dp]
             L.orc_time_integrals.restype = None
             L.orc_stencils.argtypes = [P(ctypes.c_int), P(ctypes.c_int)]
+            L.orc_char_basis.argtypes = [cp, dp, ctypes.c_int, dp, dp]
+            L.orc_char_basis.restype = ctypes.c_int
             L.orc_stencils.restype = None
             L.orc_threads_used.argtypes = [cp]
             L.orc_threads_used.restype = ctypes.c_int
@@ -268,6 +272,17 @@ def stencils():
     P = ctypes.POINTER(ctypes.c_int)
     lib().orc_stencils(big.ctypes.data_as(P), sub.ctypes.data_as(P))
     return big.reshape(18, 3), sub.reshape(24, 4, 3)
+
+
+def char_basis(cfg: Cfg, W, d: int):
+    """(R, L): right eigenvectors (columns) of the Euler flux Jacobian along
+    axis d at the conservative state W, and L = R^{-1}."""
+    W = _f64(W)
+    R = np.zeros(25)
+    L = np.zeros(25)
+    if lib().orc_char_basis(ctypes.byref(cfg), _dp(W), int(d), _dp(R), _dp(L)) != 0:
+        raise RuntimeError("oracle char basis failed")
+    return R.reshape(5, 5), L.reshape(5, 5)
 
 
 def threads_used(cfg: Cfg) -> int:

@@ -53,6 +53,7 @@ typedef struct {
     double tau_eps, tau_C; /* collision-time constants (Sec. 4)              */
     int limiter;       /* positivity fallback on/off                         */
     int nthreads;      /* OpenMP threads (0 = runtime default)               */
+    int charvar;       /* 1: reconstruct characteristic variables (Sec. 4)   */
 } orc_cfg;
 
 #ifdef _OPENMP
@@ -487,7 +488,31 @@ static double poly_value(const cell_rec *r, const double *coef, double qc, int n
     return v;
 }
 
+/* Reconstruction of cell (i,j,k).  With P (5x5, row-major) the data are
+ * the projected variables P Q of every cell of the stencil (the
+ * characteristic variables of Sec. 4, P = R^{-1}); the polynomials are then
+ * built, weighted and combined per projected variable and mapped back with
+ * Rb (= R) before the positivity check, so that r holds conservative
+ * polynomials and the indicators and weights of the projected ones. */
+static void reconstruct_cell_proj(const orc_cfg *c, const orc_geom *G, const double *Qp, int i, int j, int k,
+                                  const double *P, const double *Rb, cell_rec *r);
+
 static void reconstruct_cell(const orc_cfg *c, const orc_geom *G, const double *Qp, int i, int j, int k, cell_rec *r)
+{
+    reconstruct_cell_proj(c, G, Qp, i, j, k, NULL, NULL, r);
+}
+
+/* value of variable v of cell id, projected by P when given */
+static double data_value(const orc_dims *D, const double *Qp, const double *P, int v, size_t id)
+{
+    if (!P) return Qp[(size_t)v * D->ncell + id];
+    double s = 0.0;
+    for (int u = 0; u < NV; ++u) s += P[v * NV + u] * Qp[(size_t)u * D->ncell + id];
+    return s;
+}
+
+static void reconstruct_cell_proj(const orc_cfg *c, const orc_geom *G, const double *Qp, int i, int j, int k,
+                                  const double *P, const double *Rb, cell_rec *r)
 {
     const orc_dims *D = &G->D;
     /* geometry of the 3x3x3 block around the cell (corners unused) */
@@ -501,7 +526,7 @@ static void reconstruct_cell(const orc_cfg *c, const orc_geom *G, const double *
     for (int d = 0; d < 3; ++d) r->cen[d] = gc->cen[d];
     r->h = gc->h;
     cell_monomial_means(gc, r->cen, r->h, r->mean);
-    for (int v = 0; v < NV; ++v) r->Qc[v] = Qp[(size_t)v * D->ncell + cid(D, i, j, k)];
+    for (int v = 0; v < NV; ++v) r->Qc[v] = data_value(D, Qp, P, v, cid(D, i, j, k));
 
     /* P0: least squares over the 18 neighbours of the big stencil; the
      * centre constraint holds exactly because every p_n has zero mean. */
@@ -513,7 +538,7 @@ static void reconstruct_cell(const orc_cfg *c, const orc_geom *G, const double *
         double mn[9];
         cell_monomial_means(BLK(off[s][0], off[s][1], off[s][2]), r->cen, r->h, mn);
         for (int m = 0; m < 9; ++m) A[s * 9 + m] = mn[m] - r->mean[m];
-        for (int v = 0; v < NV; ++v) B[s * NV + v] = Qp[(size_t)v * D->ncell + cid(D, ii, jj, kk)] - r->Qc[v];
+        for (int v = 0; v < NV; ++v) B[s * NV + v] = data_value(D, Qp, P, v, cid(D, ii, jj, kk)) - r->Qc[v];
     }
     lsq_householder(ns, 9, A, NV, B, X);
     for (int v = 0; v < NV; ++v)
@@ -529,7 +554,7 @@ static void reconstruct_cell(const orc_cfg *c, const orc_geom *G, const double *
             double mn[9];
             cell_monomial_means(BLK(so[s][rr][0], so[s][rr][1], so[s][rr][2]), r->cen, r->h, mn);
             for (int m = 0; m < 3; ++m) As[rr * 3 + m] = mn[m] - r->mean[m];
-            for (int v = 0; v < NV; ++v) Bs[rr * NV + v] = Qp[(size_t)v * D->ncell + cid(D, ii, jj, kk)] - r->Qc[v];
+            for (int v = 0; v < NV; ++v) Bs[rr * NV + v] = data_value(D, Qp, P, v, cid(D, ii, jj, kk)) - r->Qc[v];
         }
         lsq_householder(4, 3, As, NV, Bs, Xs);
         for (int v = 0; v < NV; ++v)
@@ -590,6 +615,34 @@ static void reconstruct_cell(const orc_cfg *c, const orc_geom *G, const double *
         for (int s = 1; s <= 24; ++s)
             for (int m = 0; m < 3; ++m)
                 r->coef[v][m] += (wb[s] - wb[0] * gam[s] / gam[0]) * r->b[s - 1][v][m];
+    }
+
+    /* back to the conservative variables: every polynomial is linear in
+     * the data, so the map acts on the averages and coefficients */
+    if (P) {
+        double t0[NV], t9[NV][9], ta[NV][9], tb[24][NV][3];
+        for (int v = 0; v < NV; ++v) {
+            t0[v] = 0.0;
+            for (int m = 0; m < 9; ++m) t9[v][m] = ta[v][m] = 0.0;
+            for (int s2 = 0; s2 < 24; ++s2)
+                for (int m = 0; m < 3; ++m) tb[s2][v][m] = 0.0;
+            for (int u = 0; u < NV; ++u) {
+                double rv = Rb[v * NV + u];
+                t0[v] += rv * r->Qc[u];
+                for (int m = 0; m < 9; ++m) {
+                    t9[v][m] += rv * r->coef[u][m];
+                    ta[v][m] += rv * r->a[u][m];
+                }
+                for (int s2 = 0; s2 < 24; ++s2)
+                    for (int m = 0; m < 3; ++m) tb[s2][v][m] += rv * r->b[s2][u][m];
+            }
+        }
+        memcpy(r->coef, t9, sizeof t9);
+        memcpy(r->a, ta, sizeof ta);
+        memcpy(r->b, tb, sizeof tb);
+        /* the cell average itself, exactly as stored */
+        for (int v = 0; v < NV; ++v) r->Qc[v] = Qp[(size_t)v * D->ncell + cid(D, i, j, k)];
+        (void)t0;
     }
 
     /* positivity fallback (Sec. 4): if rho or p of any P_m, m = 0..24, is
@@ -1237,10 +1290,55 @@ static double face_swept_rate(const orc_geom *G, int d, int i, int j, int k)
  * and dR/dt for every interior cell, plus the grid's volume rate V = sum
  * of swept rates (zero on a fixed mesh).  L = R/|Omega| on a fixed mesh.
  * Only the cells listed in `cells` are computed when ncells >= 0. */
+/* Right eigenvectors of the Euler flux Jacobian n . dF/dQ for n = e_d at
+ * the state W (columns of R, row-major 5x5): the acoustic waves u_n -+ c,
+ * the entropy wave and the two shear waves along the tangents e_{d+1},
+ * e_{d+2}; L = R^{-1} by Gaussian elimination.  Characteristic variables
+ * are L Q (Sec. 4). */
+int orc_char_basis(const orc_cfg *c, const double *W, int d, double *Rm, double *Lm)
+{
+    double rho = W[0], u[3] = {W[1] / rho, W[2] / rho, W[3] / rho};
+    double p = pressure_of(c, W);
+    if (!(rho > 0.0) || !(p > 0.0)) return -1;
+    double cs = sqrt(c->gamma * p / rho), H = (W[4] + p) / rho, k = 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    int a = (d + 1) % 3, b = (d + 2) % 3;
+    double col[NV][NV];
+    for (int m = 0; m < NV; ++m)
+        for (int v = 0; v < NV; ++v) col[m][v] = 0.0;
+    /* u_n - c */
+    col[0][0] = 1.0;
+    for (int e = 0; e < 3; ++e) col[0][1 + e] = u[e] - (e == d ? cs : 0.0);
+    col[0][4] = H - cs * u[d];
+    /* entropy */
+    col[1][0] = 1.0;
+    for (int e = 0; e < 3; ++e) col[1][1 + e] = u[e];
+    col[1][4] = k;
+    /* shear along e_a and e_b */
+    col[2][1 + a] = 1.0;
+    col[2][4] = u[a];
+    col[3][1 + b] = 1.0;
+    col[3][4] = u[b];
+    /* u_n + c */
+    col[4][0] = 1.0;
+    for (int e = 0; e < 3; ++e) col[4][1 + e] = u[e] + (e == d ? cs : 0.0);
+    col[4][4] = H + cs * u[d];
+    for (int v = 0; v < NV; ++v)
+        for (int m = 0; m < NV; ++m) Rm[v * NV + m] = col[m][v];
+    for (int m = 0; m < NV; ++m) {
+        double e[NV] = {0, 0, 0, 0, 0}, x[NV];
+        e[m] = 1.0;
+        if (gauss_solve(NV, Rm, e, x)) return -1;
+        for (int v = 0; v < NV; ++v) Lm[v * NV + m] = x[v];
+    }
+    return 0;
+}
+
 static int residuals(const orc_cfg *c, const orc_geom *G, const double *q, double dt,
                      double *R, double *dR, double *V, long ncells, const long *cells)
 {
     const orc_dims *D = &G->D;
+    /* characteristic variables along the face normal: axis-aligned faces */
+    if (c->charvar && c->mesh != 0) return -1;
     size_t nint = (size_t)c->n[0] * c->n[1] * c->n[2];
     double *Qp = (double *)malloc(D->ncell * NV * sizeof(double));
     long *slot = (long *)malloc(D->ncell * sizeof(long));
@@ -1272,7 +1370,7 @@ static int residuals(const orc_cfg *c, const orc_geom *G, const double *q, doubl
     for (long lin = 0; lin < nrec; ++lin) {
         int i = (int)(lin % nx1) - 1, j = (int)((lin / nx1) % ny1) - 1, k = (int)(lin / ((long)nx1 * ny1)) - 1;
         size_t id = cid(D, i, j, k);
-        if (need[id]) {
+        if (need[id] && !c->charvar) {
             cell_rec full;
             reconstruct_cell(c, G, Qp, i, j, k, &full);
             slim_from(&full, &rec[slot[id]]);
@@ -1314,8 +1412,27 @@ static int residuals(const orc_cfg *c, const orc_geom *G, const double *q, doubl
         int o3[3] = {(int)(r0 % ext[0]), (int)((r0 / ext[0]) % ext[1]), (int)(r0 / ((long)ext[0] * ext[1]))};
         int l3[3] = {o3[0], o3[1], o3[2]};
         l3[d] -= 1;
-        if (face_flux(c, G, &rec[slot[cid(D, l3[0], l3[1], l3[2])]], &rec[slot[cid(D, o3[0], o3[1], o3[2])]], d, o3[0], o3[1],
-                      o3[2], dt, &FF[fid * 2 * NV], &FF[fid * 2 * NV + NV]))
+        if (c->charvar) {
+            /* characteristic variables of this face (Sec. 4): the basis of
+             * the Jacobian along the face normal at the mean of the two
+             * cell averages (reading), both sides reconstructed in it */
+            size_t idl = cid(D, l3[0], l3[1], l3[2]), idr = cid(D, o3[0], o3[1], o3[2]);
+            double Wm[NV], Rm[NV * NV], Lm[NV * NV];
+            for (int v = 0; v < NV; ++v) Wm[v] = 0.5 * (Qp[(size_t)v * D->ncell + idl] + Qp[(size_t)v * D->ncell + idr]);
+            slim_rec sl, sr;
+            if (orc_char_basis(c, Wm, d, Rm, Lm)) {
+                err = 1;
+            } else {
+                cell_rec full;
+                reconstruct_cell_proj(c, G, Qp, l3[0], l3[1], l3[2], Lm, Rm, &full);
+                slim_from(&full, &sl);
+                reconstruct_cell_proj(c, G, Qp, o3[0], o3[1], o3[2], Lm, Rm, &full);
+                slim_from(&full, &sr);
+                if (face_flux(c, G, &sl, &sr, d, o3[0], o3[1], o3[2], dt, &FF[fid * 2 * NV], &FF[fid * 2 * NV + NV]))
+                    err = 1;
+            }
+        } else if (face_flux(c, G, &rec[slot[cid(D, l3[0], l3[1], l3[2])]], &rec[slot[cid(D, o3[0], o3[1], o3[2])]], d,
+                             o3[0], o3[1], o3[2], dt, &FF[fid * 2 * NV], &FF[fid * 2 * NV + NV]))
             err = 1;
         SW[fid] = face_swept_rate(G, d, o3[0], o3[1], o3[2]);
     }
