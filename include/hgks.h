@@ -90,7 +90,17 @@ int hgks_create(const hgks_grid_t *grid, double gamma, double mu, double Pr, con
 /* Change a scheme constant: "Gamma" (linear weight of each of the 24
  * sub-stencils, Sec. 2), "weno_eps", "weno_pow" (1 or 2, exponent of
  * tau/(beta + eps) in eq. nonlinear), "tau_eps", "tau_C" (collision time,
- * Sec. 4), "limiter" (1/0: positivity fallback of Sec. 4). */
+ * Sec. 4), "limiter" (1/0: positivity fallback of Sec. 4),
+ * "characteristic" (1/0: reconstruct the characteristic variables L Q of
+ * Sec. 4, L the inverse of the right eigenvectors of the Euler flux
+ * Jacobian along the face normal at the mean of the face's two cell
+ * averages; both sides of every face are reconstructed in that basis, so
+ * the reconstruction costs about six times the conservative one and the
+ * handle allocates 2 x 50 values per face in the working precision;
+ * uniform mesh only, HGKS_E_INVALID otherwise; hgks_reconstruct then
+ * returns HGKS_E_STATE, the polynomials being per face and side).
+ * Returns HGKS_E_INVALID for an unknown key or value, HGKS_E_NOMEM when
+ * the characteristic buffers cannot be allocated. */
 int hgks_set_option(hgks_t *h, const char *key, double value);
 
 /* Load the state q ([5][nz][ny][nx] FP64, copied) at time t.  On a mapped

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhgks.so")
-SOURCES = ["hgks_kernels.cu", "hgks_mapped.cu", "hgks_api.cu", "hgks_noalloc.cu", "hgks_batch.cu"]
+SOURCES = ["hgks_kernels.cu", "hgks_mapped.cu", "hgks_char.cu", "hgks_api.cu", "hgks_noalloc.cu", "hgks_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr"]

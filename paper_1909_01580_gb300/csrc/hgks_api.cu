@@ -12,6 +12,7 @@
 #include "hgks_kernels.cuh"
 #include "hgks_mapped.cuh"
 #include "hgks_mapped_launch.cuh"
+#include "hgks_char_launch.cuh"
 
 using hk::Ctl;
 using hk::Geo;
@@ -36,6 +37,10 @@ struct hgks {
     double *geo;                 // [NGEO][pstride] cell geometry at the stage time
     double *vol, *vnext;         // [ncell] volumes of the discrete conservation law
     double *sintab;              // sine factors of the map at the vertex indices
+    // reconstruction in characteristic variables (option "characteristic")
+    int charvar;
+    void *coefc[3];              // per axis [2][50][nface_d] in the working precision
+    unsigned char *flagc[3];     // per axis [2][nface_d]
     bool have_state;
     // optional per-phase timing with CUDA events on the handle's stream
     bool timing;
@@ -149,6 +154,10 @@ static void free_all(hgks_t *h)
     cudaFree(h->vol);
     cudaFree(h->vnext);
     cudaFree(h->sintab);
+    for (int d = 0; d < 3; ++d) {
+        cudaFree(h->coefc[d]);
+        cudaFree(h->flagc[d]);
+    }
 }
 
 extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, double Pr, const int bc[6], void *stream,
@@ -328,6 +337,32 @@ extern "C" int hgks_set_option(hgks_t *h, const char *key, double value)
         h->S.tau_C = value;
     } else if (!strcmp(key, "limiter")) {
         h->S.limiter = value != 0.0;
+    } else if (!strcmp(key, "characteristic")) {
+        if (value != 0.0 && value != 1.0) return fail(h, HGKS_E_INVALID, "characteristic must be 0 or 1%s");
+        if (value == 1.0 && h->mesh != 0)
+            return fail(h, HGKS_E_INVALID, "characteristic variables need the uniform mesh%s");
+        if (value == 1.0 && !h->coefc[0]) {
+            const Geo &g = h->g;
+            const size_t elem = h->precision == HGKS_MIXED ? sizeof(float) : sizeof(double);
+            for (int d = 0; d < 3; ++d) {
+                const size_t nface = (size_t)(g.nx + (d == 0)) * (g.ny + (d == 1)) * (g.nz + (d == 2));
+                const size_t bc = 2 * hk::CHAR_SLOTS_API * nface * elem, bf = 2 * nface;
+                if (cudaMalloc(&h->coefc[d], bc) != cudaSuccess || cudaMalloc((void **)&h->flagc[d], bf) != cudaSuccess) {
+                    cudaGetLastError();
+                    for (int e = 0; e <= d; ++e) {
+                        cudaFree(h->coefc[e]);
+                        cudaFree(h->flagc[e]);
+                        h->coefc[e] = nullptr;
+                        h->flagc[e] = nullptr;
+                    }
+                    return fail(h, HGKS_E_NOMEM, "characteristic buffers: device allocation failed%s");
+                }
+                CUDA_OK(h, cudaMemsetAsync(h->coefc[d], 0, bc, h->stream));
+                CUDA_OK(h, cudaMemsetAsync(h->flagc[d], 0, bf, h->stream));
+                h->bytes += bc + bf;
+            }
+        }
+        h->charvar = value == 1.0;
     } else {
         return fail(h, HGKS_E_INVALID, "unknown option %s", key);
     }
@@ -423,6 +458,28 @@ static int stage_fluxes(hgks_t *h, double *Q, int half = 0, bool geom_ready = fa
     {
         PhaseTimer t(h, HGKS_PHASE_HALO, 1);
         hk::launch_halo(Q, g, s);
+    }
+    if (h->charvar) {
+        // characteristic variables: both sides of every face reconstructed
+        // in the face's eigenbasis (and the literal positivity pass), then
+        // the face fluxes from those polynomials
+        {
+            PhaseTimer t(h, HGKS_PHASE_RECON, 6);
+            for (int d = 0; d < 3; ++d) {
+                if (h->precision == HGKS_MIXED)
+                    hk::launch_recon_char<float>(d, Q, (float *)h->coefc[d], h->flagc[d], g, h->S, h->ctl, s);
+                else
+                    hk::launch_recon_char<double>(d, Q, (double *)h->coefc[d], h->flagc[d], g, h->S, h->ctl, s);
+            }
+        }
+        PhaseTimer t(h, HGKS_PHASE_FLUX, 3);
+        for (int d = 0; d < 3; ++d) {
+            if (h->precision == HGKS_MIXED)
+                hk::launch_flux_char<float>(d, (const float *)h->coefc[d], h->F[d], g, h->S, h->ctl, s);
+            else
+                hk::launch_flux_char<double>(d, (const double *)h->coefc[d], h->F[d], g, h->S, h->ctl, s);
+        }
+        return check_launch(h, 10);
     }
     if (h->precision == HGKS_MIXED) {
         float *c = (float *)h->coef;
@@ -552,6 +609,9 @@ extern "C" int hgks_reconstruct(hgks_t *h, double *coef, int *flag)
 {
     if (!h || !coef) return HGKS_E_INVALID;
     if (!h->have_state) return fail(h, HGKS_E_STATE, "no state loaded%s");
+    if (h->charvar)
+        return fail(h, HGKS_E_STATE, "per-cell polynomials do not exist with characteristic variables (they are "
+                                     "per face and side)%s");
     const Geo &g = h->g;
     cudaStream_t s = h->stream;
     CUDA_OK(h, cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));

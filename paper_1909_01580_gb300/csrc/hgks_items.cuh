@@ -161,8 +161,8 @@ __device__ __forceinline__ void recon_item(const double *__restrict__ Q, R *__re
 // the faces computes a clamped face and writes nothing.
 // ---------------------------------------------------------------------------
 template <typename R, int D>
-__device__ __forceinline__ void eval_side(const R *__restrict__ coef, const Geo &g, long long ci, R xd, R xa, R xb,
-                                          R W[5], R dW[3][5])
+__device__ __forceinline__ void eval_side(const R *__restrict__ coef, long long stride, long long ci, const Geo &g,
+                                          R xd, R xa, R xb, R W[5], R dW[3][5])
 {
     // at a face Gauss point the face-normal coordinate is xd = +-1/2 and the
     // tangential ones are +-1/(2 sqrt 3), so the zero-mean tangential squares
@@ -177,8 +177,8 @@ __device__ __forceinline__ void eval_side(const R *__restrict__ coef, const Geo 
     for (int v = 0; v < 5; ++v) {
         R c[9];
 #pragma unroll
-        for (int n = 0; n < 9; ++n) c[n] = coef[coef_slot(v, 1 + n) * g.cstride + ci];
-        val[v] = coef[coef_slot(v, 0) * g.cstride + ci] + (c[D] * xd + c[3 + D] * R(1.0 / 6.0)) +
+        for (int n = 0; n < 9; ++n) c[n] = coef[coef_slot(v, 1 + n) * stride + ci];
+        val[v] = coef[coef_slot(v, 0) * stride + ci] + (c[D] * xd + c[3 + D] * R(1.0 / 6.0)) +
                  xa * (c[A] + c[DA] * xd) + xb * (c[B] + c[DB] * xd) + c[AB] * xa * xb;
         grad[v][D] = (c[D] + R(2) * c[3 + D] * xd + c[DA] * xa + c[DB] * xb) * ih;
         grad[v][A] = (c[A] + R(2) * c[3 + A] * xa + c[DA] * xd + c[AB] * xb) * ih;
@@ -204,7 +204,9 @@ template <int D> __device__ __forceinline__ long long face_count(const Geo &g)
     return (long long)(g.nx + (D == 0)) * (g.ny + (D == 1)) * (g.nz + (D == 2));
 }
 
-template <typename R, int D>
+// CH: the polynomials are per (face, side) in the layout of hgks_char.cuh
+// ([side][slot][face], coef pointing at the axis's array) instead of per cell
+template <typename R, int D, bool CH = false>
 __device__ __forceinline__ void flux_item(const R *__restrict__ coef, double *__restrict__ Fout, const Geo &g,
                                           const Scheme &S, double dt, long long t, long long tlimit = LLONG_MAX)
 {
@@ -220,8 +222,13 @@ __device__ __forceinline__ void flux_item(const R *__restrict__ coef, double *__
     const R xa = (gp & 2) ? R(GAUSS_S) : R(-GAUSS_S);
     const R xb = (gp & 1) ? R(GAUSS_S) : R(-GAUSS_S);
     R Wl[5], dWl[3][5], Wr[5], dWr[3][5];
-    eval_side<R, D>(coef, g, cidx(g, il, jl, kl), R(0.5), xa, xb, Wl, dWl);
-    eval_side<R, D>(coef, g, cidx(g, i, j, k), R(-0.5), xa, xb, Wr, dWr);
+    if (CH) {
+        eval_side<R, D>(coef, nface, face, g, R(0.5), xa, xb, Wl, dWl);
+        eval_side<R, D>(coef + 50 * nface, nface, face, g, R(-0.5), xa, xb, Wr, dWr);
+    } else {
+        eval_side<R, D>(coef, g.cstride, cidx(g, il, jl, kl), g, R(0.5), xa, xb, Wl, dWl);
+        eval_side<R, D>(coef, g.cstride, cidx(g, i, j, k), g, R(-0.5), xa, xb, Wr, dWr);
+    }
     R F[5], dF[5];
     gks_flux<R>(Wl, dWl, Wr, dWr, S, R(dt), F, dF);
     // back to the global frame, Gauss weight 1/4, sum of the 4 lanes in the
