@@ -90,8 +90,12 @@ int hgks_create(const hgks_grid_t *grid, double gamma, double mu, double Pr, con
 /* Change a scheme constant: "Gamma" (linear weight of each of the 24
  * sub-stencils, Sec. 2), "weno_eps", "weno_pow" (1 or 2, exponent of
  * tau/(beta + eps) in eq. nonlinear), "tau_eps", "tau_C" (collision time,
- * Sec. 4), "limiter" (1/0: positivity fallback of Sec. 4),
- * "characteristic" (1/0: reconstruct the characteristic variables L Q of
+ * Sec. 4), "limiter" (1/0: positivity fallback of Sec. 4), "mu_power" and
+ * "mu_T_ref" (viscosity law mu (T/T_ref)^mu_power of the isotropic
+ * turbulence of Sec. 4, 0.76 there, evaluated at the temperature p/rho of
+ * the interface equilibrium state in the collision time; mu_power = 0, the
+ * default, keeps mu constant), "characteristic" (1/0: reconstruct the
+ * characteristic variables L Q of
  * Sec. 4, L the inverse of the right eigenvectors of the Euler flux
  * Jacobian along the face normal at the mean of the face's two cell
  * averages; both sides of every face are reconstructed in that basis, so

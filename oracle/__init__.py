@@ -61,12 +61,15 @@ class Cfg(ctypes.Structure):
         ("limiter", ctypes.c_int),
         ("nthreads", ctypes.c_int),
         ("charvar", ctypes.c_int),
+        ("mu_pow", ctypes.c_double),
+        ("T_ref", ctypes.c_double),
     ]
 
 
 def make_cfg(n, lo=(0.0, 0.0, 0.0), hi=(2.0, 2.0, 2.0), *, gamma=1.4, mu=0.0, Pr=1.0,
              bc=(0, 0, 0, 0, 0, 0), mesh=0, amp=0.0, omega=0.0, Gamma_lin=0.0025,
-             weno_eps=1e-8, weno_pow=1, tau_eps=0.01, tau_C=1.0, limiter=1, nthreads=0, charvar=0) -> Cfg:
+             weno_eps=1e-8, weno_pow=1, tau_eps=0.01, tau_C=1.0, limiter=1, nthreads=0, charvar=0,
+             mu_pow=0.0, T_ref=1.0) -> Cfg:
     """Configuration with the paper's defaults (Gamma = 0.0025, tau constants
     eps = 0.01 and C = 1 of Sec. 4, gamma = 1.4)."""
     c = Cfg()
@@ -82,6 +85,7 @@ def make_cfg(n, lo=(0.0, 0.0, 0.0), hi=(2.0, 2.0, 2.0), *, gamma=1.4, mu=0.0, Pr
     c.tau_eps, c.tau_C = float(tau_eps), float(tau_C)
     c.limiter, c.nthreads = int(limiter), int(nthreads)
     c.charvar = int(charvar)
+    c.mu_pow, c.T_ref = float(mu_pow), float(T_ref)
     return c
 
 

@@ -54,6 +54,9 @@ typedef struct {
     int limiter;       /* positivity fallback on/off                         */
     int nthreads;      /* OpenMP threads (0 = runtime default)               */
     int charvar;       /* 1: reconstruct characteristic variables (Sec. 4)   */
+    double mu_pow;     /* mu = mu (T/T_ref)^mu_pow (isotropic turbulence,
+                          Sec. 4: 0.76); 0 keeps mu constant                   */
+    double T_ref;      /* reference temperature p/rho of that law            */
 } orc_cfg;
 
 #ifdef _OPENMP
@@ -1027,7 +1030,11 @@ int orc_point_flux(const orc_cfg *c, const double *in, const double *ug, double 
     double pl = pressure_of(c, W[0]), pr = pressure_of(c, W[1]);
     double jump = fabs((pl - pr) / (pl + pr));
     double tau;
-    if (c->mu > 0.0) tau = c->mu / (g0.rho / (2.0 * g0.lam)) + c->tau_C * jump * dt;
+    /* viscosity at the interface: mu, or mu (T0/T_ref)^mu_pow with T0 = p0/rho0
+     * = 1/(2 lam0) the temperature of g0 */
+    double mu_eff = c->mu;
+    if (c->mu_pow != 0.0) mu_eff = c->mu * pow(1.0 / (2.0 * g0.lam) / c->T_ref, c->mu_pow);
+    if (c->mu > 0.0) tau = mu_eff / (g0.rho / (2.0 * g0.lam)) + c->tau_C * jump * dt;
     else tau = c->tau_eps * dt + c->tau_C * jump * dt;
 
     /* weight polynomials of the time-integrated distribution (kept on the

@@ -337,6 +337,12 @@ extern "C" int hgks_set_option(hgks_t *h, const char *key, double value)
         h->S.tau_C = value;
     } else if (!strcmp(key, "limiter")) {
         h->S.limiter = value != 0.0;
+    } else if (!strcmp(key, "mu_power")) {
+        if (!(value >= 0.0) || !(value <= 4.0)) return fail(h, HGKS_E_INVALID, "mu_power must be in [0, 4]%s");
+        h->S.mu_pow = value;
+    } else if (!strcmp(key, "mu_T_ref")) {
+        if (!(value > 0.0)) return fail(h, HGKS_E_INVALID, "mu_T_ref must be > 0%s");
+        h->S.T_ref = value;
     } else if (!strcmp(key, "characteristic")) {
         if (value != 0.0 && value != 1.0) return fail(h, HGKS_E_INVALID, "characteristic must be 0 or 1%s");
         if (value == 1.0 && h->mesh != 0)

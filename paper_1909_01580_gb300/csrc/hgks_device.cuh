@@ -37,6 +37,8 @@ HK_HD double m_abs(double x) { return fabs(x); }
 HK_HD double m_max(double a, double b) { return fmax(a, b); }
 HK_HD float m_max(float a, float b) { return fmaxf(a, b); }
 HK_HD float m_abs(float x) { return fabsf(x); }
+HK_HD double m_pow(double x, double y) { return pow(x, y); }
+HK_HD float m_pow(float x, float y) { return powf(x, y); }
 
 // Constants of the Gauss-point flux in one working precision, derived on the
 // host (scheme_derive) so that no thread converts or divides them.
@@ -45,6 +47,7 @@ template <typename R> struct FluxK {
     R mu2;                       // 2 mu
     R tau_eps, tau_C;
     R prfac;                     // 1/Pr - 1
+    R mu_pow, iT_ref;            // viscosity law mu (T/T_ref)^mu_pow
 };
 
 // Scheme constants, passed by value to every kernel.  After any change of
@@ -58,6 +61,8 @@ struct Scheme {
     double Gamma_lin;  // linear weight of each sub-stencil
     int weno_pow;      // exponent on tau/(beta + eps)
     int limiter;       // positivity fallback on/off
+    double mu_pow = 0.0;  // viscosity law mu (T/T_ref)^mu_pow (0: constant mu)
+    double T_ref = 1.0;   // reference temperature p/rho of that law
     int viscous;       // mu > 0
     int prfix;         // mu > 0 and Pr != 1: Prandtl correction of the energy flux
     FluxK<double> kd;
@@ -75,6 +80,8 @@ template <typename R> HK_HD void fluxk_fill(const Scheme &S, FluxK<R> &k)
     k.tau_eps = R(S.tau_eps);
     k.tau_C = R(S.tau_C);
     k.prfac = R(1.0 / S.Pr - 1.0);
+    k.mu_pow = R(S.mu_pow);
+    k.iT_ref = R(1.0 / S.T_ref);
 }
 
 inline void scheme_derive(Scheme &S)
@@ -479,8 +486,13 @@ HK_HD void gks_flux(const R Wl[5], const R dWl[3][5], const R Wr[5], const R dWr
     // collision time (Sec. 4)
     R jump = m_abs((pside[0] - pside[1]) / (pside[0] + pside[1]));
     R tau;
-    if (S.viscous)
-        tau = C.mu2 * s0.lam * s0.ir + C.tau_C * jump * dt;  // mu/p0, p0 = rho0/(2 lam0)
+    if (S.viscous) {
+        // mu/p0 with p0 = rho0/(2 lam0); with the viscosity law, mu at the
+        // temperature T0 = p0/rho0 = 1/(2 lam0) of g0
+        R mu2 = C.mu2;
+        if (S.mu_pow != 0.0) mu2 *= m_pow(s0.th * C.iT_ref, C.mu_pow);
+        tau = mu2 * s0.lam * s0.ir + C.tau_C * jump * dt;
+    }
     else
         tau = (C.tau_eps + C.tau_C * jump) * dt;
 

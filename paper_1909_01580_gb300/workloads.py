@@ -166,6 +166,92 @@ def blast_wave(n, lo=(0.0, 0.0, 0.0), hi=(100.0, 10.0, 10.0), gamma=1.4, p_mid=0
     return np.ascontiguousarray(np.broadcast_to(line[:, None, None, :], (5, n[2], n[1], n[0])), dtype=np.float64)
 
 
+@dataclass
+class TurbulenceParams:
+    """Constants of the isotropic-turbulence workload (Sec. 4)."""
+    A0: float
+    k0: float
+    u_rms: float
+    K0: float          # initial turbulent kinetic energy (per unit mass)
+    T0: float          # temperature p/rho (R = 1)
+    p0: float
+    mu0: float         # viscosity at T0; mu = mu0 (T/T0)^0.76
+    tau_t0: float      # large-eddy-turnover time
+
+
+def isotropic_turbulence(n, mach_t, seed=0, A0=1.3e-4, k0=8.0, re_lambda=72.0, gamma=1.4, rho0=1.0):
+    """Compressible isotropic turbulence of Sec. 4 on [-pi, pi]^3: a seeded
+    divergence-free random velocity with the spectrum E(k) = A0 k^4
+    exp(-2 k^2/k0^2), uniform density rho0 and temperature T0 set by the
+    turbulent Mach number Ma_t = sqrt(3) u_rms/sqrt(gamma T0), viscosity
+    mu0 from the Taylor Reynolds number Re_lambda = (2 pi)^(1/4)/4 rho0/mu0
+    sqrt(2 A0) k0^(3/2).  Every Fourier mode has the amplitude of the
+    spectrum (|u_k|^2 = E(k)/(2 pi k^2)), a random direction normal to k
+    and a random phase; the field is scaled to the u_rms of the continuous
+    spectrum, u_rms^2 = 2 K0/3, K0 = 3 A0 sqrt(2 pi) k0^5/64.  Velocities are
+    exact cell averages of that Fourier field (each mode times the cell's
+    sinc factors); rho E uses the averaged velocity (reading).
+    Returns (q, lo, hi, TurbulenceParams)."""
+    rng = np.random.default_rng(seed)
+    N = int(n)
+    lo, hi = (-math.pi,) * 3, (math.pi,) * 3
+    h = 2 * math.pi / N
+    k1 = np.fft.fftfreq(N, d=1.0 / N)  # integer wavenumbers on a 2 pi box
+    KZ, KY, KX = np.meshgrid(k1, k1, k1, indexing="ij")
+    kk = np.sqrt(KX ** 2 + KY ** 2 + KZ ** 2)
+    # random real field per component -> divergence-free part -> amplitudes
+    uh = [np.fft.fftn(rng.standard_normal((N, N, N))) for _ in range(3)]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        kdotu = (KX * uh[0] + KY * uh[1] + KZ * uh[2]) / np.where(kk > 0, kk * kk, 1.0)
+        uh = [uh[0] - KX * kdotu, uh[1] - KY * kdotu, uh[2] - KZ * kdotu]
+        mag = np.sqrt(np.abs(uh[0]) ** 2 + np.abs(uh[1]) ** 2 + np.abs(uh[2]) ** 2)
+        E = A0 * kk ** 4 * np.exp(-2.0 * kk ** 2 / k0 ** 2)
+        amp = np.where((kk > 0) & (mag > 0), np.sqrt(E / (2 * math.pi * np.where(kk > 0, kk * kk, 1.0))) /
+                       np.where(mag > 0, mag, 1.0), 0.0)
+    # no Nyquist modes: their projection would break the symmetry of a real field
+    nyq = (np.abs(KX) == N // 2) | (np.abs(KY) == N // 2) | (np.abs(KZ) == N // 2)
+    amp = np.where(nyq, 0.0, amp)
+    # FFT convention u(x) = sum_k u_k exp(i k x) with u_k = fftn(u) / N^3
+    sinc = 1.0
+    for K in (KX, KY, KZ):
+        a = 0.5 * K * h
+        sinc = sinc * np.where(a == 0, 1.0, np.sin(a) / np.where(a == 0, 1.0, a))
+    u_pt = [np.real(np.fft.ifftn(uh[d] * amp)) * N ** 3 for d in range(3)]  # point values
+    u_av = [np.real(np.fft.ifftn(uh[d] * amp * sinc)) * N ** 3 for d in range(3)]
+    K0 = 3.0 * A0 * math.sqrt(2 * math.pi) * k0 ** 5 / 64.0
+    u_rms = math.sqrt(2.0 * K0 / 3.0)
+    scale = u_rms / math.sqrt(np.mean(u_pt[0] ** 2 + u_pt[1] ** 2 + u_pt[2] ** 2) / 3.0)
+    u_av = [u * scale for u in u_av]
+    T0 = 3.0 * u_rms ** 2 / (gamma * mach_t ** 2)
+    p0 = rho0 * T0
+    mu0 = (2 * math.pi) ** 0.25 / 4.0 * rho0 * math.sqrt(2 * A0) * k0 ** 1.5 / re_lambda
+    tau_t0 = math.sqrt(32.0 / A0) * (2 * math.pi) ** 0.25 * k0 ** -3.5
+    rho = np.full((N, N, N), rho0)
+    q = np.stack([rho, rho * u_av[0], rho * u_av[1], rho * u_av[2],
+                  p0 / (gamma - 1.0) + 0.5 * rho * (u_av[0] ** 2 + u_av[1] ** 2 + u_av[2] ** 2)]).astype(np.float64)
+    return q, lo, hi, TurbulenceParams(A0, k0, u_rms, K0, T0, p0, mu0, tau_t0)
+
+
+def turbulence_stats(q, gamma=1.4):
+    """Volume statistics of a periodic cubic state: turbulent kinetic energy
+    K = <rho |u|^2>/(2 <rho>), rho_rms, the velocity-derivative skewness
+    S_u = <(du_i/dx_i)^3>/<(du_i/dx_i)^2>^(3/2) (mean over i, spectral
+    derivatives on a 2 pi box) and the divergence rms."""
+    rho = q[0]
+    u = [q[1 + d] / rho for d in range(3)]
+    K = float(np.mean(rho * (u[0] ** 2 + u[1] ** 2 + u[2] ** 2)) / (2.0 * np.mean(rho)))
+    rho_rms = float(np.sqrt(np.mean((rho - rho.mean()) ** 2)))
+    N = rho.shape[0]
+    k1 = np.fft.fftfreq(N, d=1.0 / N)
+    kz, ky, kx = np.meshgrid(k1, k1, k1, indexing="ij")
+    ks = (kx, ky, kz)
+    dii = [np.real(np.fft.ifftn(1j * ks[d] * np.fft.fftn(u[d]))) for d in range(3)]
+    s3 = np.mean([np.mean(x ** 3) for x in dii])
+    s2 = np.mean([np.mean(x ** 2) for x in dii])
+    div = dii[0] + dii[1] + dii[2]
+    return {"K": K, "rho_rms": rho_rms, "skewness": float(s3 / s2 ** 1.5), "div_rms": float(np.sqrt(np.mean(div ** 2)))}
+
+
 def taylor_green(n, mach=0.1, gamma=1.4, L=1.0, V0=1.0, rho0=1.0):
     """Taylor-Green vortex on [-pi L, pi L]^3 (Sec. 4): u = V0 sin x cos y cos z,
     v = -V0 cos x sin y cos z, w = 0, p = p0 + rho0 V0^2/16 (cos 2x + cos 2y)(cos 2z + 2).

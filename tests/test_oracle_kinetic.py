@@ -331,3 +331,24 @@ def test_navier_stokes_limit(Pr):
     dTdx = -p / rho ** 2 * r
     kappa = mu * GAMMA / ((GAMMA - 1) * Pr)
     assert abs(F2[4] - (-kappa * dTdx)) < 2e-3 * abs(kappa * dTdx), (F2[4], -kappa * dTdx)
+
+
+@pytest.mark.parametrize("rho,p", [(1.0, 1.0), (0.8, 2.5), (1.6, 0.4)])
+def test_navier_stokes_limit_power_law_viscosity(rho, p):
+    """Isotropic-turbulence viscosity law mu(T) = mu_ref (T/T_ref)^0.76 (Sec.
+    4): in the Navier-Stokes limit the shear stress is -mu(T) dV/dx with T =
+    p/rho of the interface state."""
+    mu_ref, T_ref, dt = 1e-4, 0.7, 0.05
+    cfg = oracle.make_cfg((4, 4, 4), mu=mu_ref, Pr=1.0, tau_C=0.0, mu_pow=0.76, T_ref=T_ref)
+    inp = np.zeros(40)
+    E = p / (GAMMA - 1)
+    inp[0:5] = inp[20:25] = [rho, 0, 0, 0, E]
+    s = 0.5
+    for side in (0, 20):
+        inp[side + 5 + 2] = s
+    F, _ = oracle.point_flux(cfg, inp, dt)
+    mu_T = mu_ref * (p / rho / T_ref) ** 0.76
+    assert abs(F[2] - (-mu_T * s / rho)) < 2e-3 * mu_T * s, (F[2], -mu_T * s / rho)
+    # the law is not the constant viscosity unless T = T_ref
+    if abs(p / rho - T_ref) > 0.1:
+        assert abs(F[2] - (-mu_ref * s / rho)) > 1e-2 * mu_ref * s
