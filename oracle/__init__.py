@@ -63,13 +63,14 @@ class Cfg(ctypes.Structure):
         ("charvar", ctypes.c_int),
         ("mu_pow", ctypes.c_double),
         ("T_ref", ctypes.c_double),
+        ("stencil", ctypes.c_int),
     ]
 
 
 def make_cfg(n, lo=(0.0, 0.0, 0.0), hi=(2.0, 2.0, 2.0), *, gamma=1.4, mu=0.0, Pr=1.0,
              bc=(0, 0, 0, 0, 0, 0), mesh=0, amp=0.0, omega=0.0, Gamma_lin=0.0025,
              weno_eps=1e-8, weno_pow=1, tau_eps=0.01, tau_C=1.0, limiter=1, nthreads=0, charvar=0,
-             mu_pow=0.0, T_ref=1.0) -> Cfg:
+             mu_pow=0.0, T_ref=1.0, stencil=0) -> Cfg:
     """Configuration with the paper's defaults (Gamma = 0.0025, tau constants
     eps = 0.01 and C = 1 of Sec. 4, gamma = 1.4)."""
     c = Cfg()
@@ -86,6 +87,7 @@ def make_cfg(n, lo=(0.0, 0.0, 0.0), hi=(2.0, 2.0, 2.0), *, gamma=1.4, mu=0.0, Pr
     c.limiter, c.nthreads = int(limiter), int(nthreads)
     c.charvar = int(charvar)
     c.mu_pow, c.T_ref = float(mu_pow), float(T_ref)
+    c.stencil = int(stencil)
     return c
 
 
@@ -123,6 +125,7 @@ def lib():
             L.orc_time_integrals.restype = None
             L.orc_stencils.argtypes = [P(ctypes.c_int), P(ctypes.c_int)]
             L.orc_char_basis.argtypes = [cp, dp, ctypes.c_int, dp, dp]
+            L.orc_stencils_sprime.argtypes = [P(ctypes.c_int), P(ctypes.c_int)]
             L.orc_char_basis.restype = ctypes.c_int
             L.orc_stencils.restype = None
             L.orc_threads_used.argtypes = [cp]
@@ -276,6 +279,15 @@ def stencils():
     P = ctypes.POINTER(ctypes.c_int)
     lib().orc_stencils(big.ctypes.data_as(P), sub.ctypes.data_as(P))
     return big.reshape(18, 3), sub.reshape(24, 4, 3)
+
+
+def stencils_sprime():
+    """(big[24][3], sub[8][3][3]): the big stencil S' and its sub-stencils."""
+    big = np.zeros(24 * 3, dtype=np.int32)
+    sub = np.zeros(8 * 3 * 3, dtype=np.int32)
+    P = ctypes.POINTER(ctypes.c_int)
+    lib().orc_stencils_sprime(big.ctypes.data_as(P), sub.ctypes.data_as(P))
+    return big.reshape(24, 3), sub.reshape(8, 3, 3)
 
 
 def char_basis(cfg: Cfg, W, d: int):

@@ -31,7 +31,7 @@
 #include <stdint.h>
 
 #define NV 5
-#define GH 2 /* ghost layers: the big stencil reaches one cell, and the
+#define GH 3 /* ghost layers: the big stencil S' reaches two cells, and the
                 reconstruction of the first ghost cell reaches one more */
 
 /* ------------------------------------------------------------------------ */
@@ -57,6 +57,8 @@ typedef struct {
     double mu_pow;     /* mu = mu (T/T_ref)^mu_pow (isotropic turbulence,
                           Sec. 4: 0.76); 0 keeps mu constant                   */
     double T_ref;      /* reference temperature p/rho of that law            */
+    int stencil;       /* 0: big stencil S and 24 sub-stencils (Sec. 2);
+                          1: S' and its 8 sub-stencils (Remark of Sec. 2)    */
 } orc_cfg;
 
 #ifdef _OPENMP
@@ -330,8 +332,11 @@ static void geom_free(orc_geom *G)
  * of the Riemann problems of Sec. 4).  Edge and corner ghosts take every
  * applicable wrap, mirror or repeat, since the big stencil reaches the edge
  * neighbours. */
-static void fill_ghosts(const orc_cfg *c, const orc_dims *D, const double *q, double *Qp)
+static int fill_ghosts(const orc_cfg *c, const orc_dims *D, const double *q, double *Qp)
 {
+    /* a mirror reaches GH cells into the grid */
+    for (int d = 0; d < 3; ++d)
+        if (c->n[d] < GH && (c->bc[2 * d] == 1 || c->bc[2 * d + 1] == 1)) return -1;
     size_t ncint = (size_t)c->n[0] * c->n[1] * c->n[2];
     for (int k = -GH; k < c->n[2] + GH; ++k)
         for (int j = -GH; j < c->n[1] + GH; ++j)
@@ -340,11 +345,11 @@ static void fill_ghosts(const orc_cfg *c, const orc_dims *D, const double *q, do
                 for (int d = 0; d < 3; ++d) {
                     int n = c->n[d], s = idx[d];
                     if (s < 0) {
-                        if (c->bc[2 * d] == 0) s += n;
+                        if (c->bc[2 * d] == 0) s = ((s % n) + n) % n;
                         else if (c->bc[2 * d] == 2) s = 0;
                         else { s = -1 - s; flip[d] = 1; }
                     } else if (s >= n) {
-                        if (c->bc[2 * d + 1] == 0) s -= n;
+                        if (c->bc[2 * d + 1] == 0) s = s % n;
                         else if (c->bc[2 * d + 1] == 2) s = n - 1;
                         else { s = 2 * n - 1 - s; flip[d] = 1; }
                     }
@@ -358,6 +363,7 @@ static void fill_ghosts(const orc_cfg *c, const orc_dims *D, const double *q, do
                     Qp[(size_t)v * D->ncell + to] = val;
                 }
             }
+    return 0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -416,8 +422,9 @@ static void cell_monomial_means(const cell_geom *g, const double *cen, double h,
     }
 }
 
-/* The big stencil S: the 3x3x3 block minus the centre and the 8 corners. */
-static int big_stencil(int off[18][3])
+/* The big stencil S: the 3x3x3 block minus the centre and the 8 corners;
+ * S' (sprime) adds the six cells two steps away along the axes. */
+static int big_stencil(int off[24][3], int sprime)
 {
     int n = 0;
     for (int k0 = -1; k0 <= 1; ++k0)
@@ -428,6 +435,13 @@ static int big_stencil(int off[18][3])
                 off[n][0] = i0; off[n][1] = j0; off[n][2] = k0;
                 ++n;
             }
+    if (sprime)
+        for (int d = 0; d < 3; ++d)
+            for (int sg = -2; sg <= 2; sg += 4) {
+                off[n][0] = off[n][1] = off[n][2] = 0;
+                off[n][d] = sg;
+                ++n;
+            }
     return n;
 }
 
@@ -436,6 +450,14 @@ static int big_stencil(int off[18][3])
  * for the plane (a,b) with out-of-plane axis c, signs (s_a, s_b, s_c) in
  * the printed order (+++), (-++), (+-+), (--+), (++-), (-+-), (+--), (---),
  * for the planes xy, yz, zx in turn ("symmetrically"). */
+/* The 8 sub-stencils of S' (sprime): the centre and one face neighbour along
+ * each axis, {s_x e_x, s_y e_y, s_z e_z}, signs in the printed order S'_1..S'_8:
+ * (+++), (-++), (+-+), (--+), (++-), (-+-), (+--), (---).  Reading: the
+ * printed S'_4 and S'_8 repeat S'_2 and S'_6; they are read as the two
+ * remaining octants (--+) and (---).  Returns the number of sub-stencils
+ * and sets the cells per sub-stencil (besides the centre) in *nrow. */
+static int sub_stencils_sel(int off[24][4][3], int *nrow, int sprime);
+
 static void sub_stencils(int off[24][4][3])
 {
     static const int SG[8][3] = {{1, 1, 1}, {-1, 1, 1}, {1, -1, 1}, {-1, -1, 1},
@@ -452,6 +474,24 @@ static void sub_stencils(int off[24][4][3])
             off[m][2][a] = SG[s][0]; off[m][2][b] = SG[s][1];
             off[m][3][cc] = SG[s][2];
         }
+}
+
+static int sub_stencils_sel(int off[24][4][3], int *nrow, int sprime)
+{
+    if (!sprime) {
+        sub_stencils(off);
+        *nrow = 4;
+        return 24;
+    }
+    static const int SG[8][3] = {{1, 1, 1}, {-1, 1, 1}, {1, -1, 1}, {-1, -1, 1},
+                                 {1, 1, -1}, {-1, 1, -1}, {1, -1, -1}, {-1, -1, -1}};
+    for (int m = 0; m < 8; ++m)
+        for (int r = 0; r < 3; ++r) {
+            for (int d = 0; d < 3; ++d) off[m][r][d] = 0;
+            off[m][r][r] = SG[m][r];
+        }
+    *nrow = 3;
+    return 8;
 }
 
 /* the 24 face Gauss points of a cell (6 faces x 2 x 2) in physical space */
@@ -518,13 +558,20 @@ static void reconstruct_cell_proj(const orc_cfg *c, const orc_geom *G, const dou
                                   const double *P, const double *Rb, cell_rec *r)
 {
     const orc_dims *D = &G->D;
-    /* geometry of the 3x3x3 block around the cell (corners unused) */
-    cell_geom blk[3][3][3];
-    for (int c2 = -1; c2 <= 1; ++c2)
-        for (int b2 = -1; b2 <= 1; ++b2)
-            for (int a2 = -1; a2 <= 1; ++a2)
-                if (a2 * b2 * c2 == 0) cell_geometry(G, i + a2, j + b2, k + c2, &blk[c2 + 1][b2 + 1][a2 + 1]);
-#define BLK(o0, o1, o2) (&blk[(o2) + 1][(o1) + 1][(o0) + 1])
+    /* geometry of the cells of the big stencil around the cell: the 3x3x3
+     * block without its corners, and for S' the axis cells two steps away */
+    static cell_geom zero_geom;
+    cell_geom blk[5][5][5];
+    for (int c2 = -2; c2 <= 2; ++c2)
+        for (int b2 = -2; b2 <= 2; ++b2)
+            for (int a2 = -2; a2 <= 2; ++a2) {
+                const int in3 = abs(a2) <= 1 && abs(b2) <= 1 && abs(c2) <= 1 && a2 * b2 * c2 == 0;
+                const int axis2 = c->stencil && abs(a2) + abs(b2) + abs(c2) == 2 &&
+                                  (abs(a2) == 2 || abs(b2) == 2 || abs(c2) == 2);
+                if (in3 || axis2) cell_geometry(G, i + a2, j + b2, k + c2, &blk[c2 + 2][b2 + 2][a2 + 2]);
+                else blk[c2 + 2][b2 + 2][a2 + 2] = zero_geom;
+            }
+#define BLK(o0, o1, o2) (&blk[(o2) + 2][(o1) + 2][(o0) + 2])
     const cell_geom *gc = BLK(0, 0, 0);
     for (int d = 0; d < 3; ++d) r->cen[d] = gc->cen[d];
     r->h = gc->h;
@@ -533,9 +580,9 @@ static void reconstruct_cell_proj(const orc_cfg *c, const orc_geom *G, const dou
 
     /* P0: least squares over the 18 neighbours of the big stencil; the
      * centre constraint holds exactly because every p_n has zero mean. */
-    int off[18][3];
-    int ns = big_stencil(off);
-    double A[18 * 9], B[18 * NV], X[9 * NV];
+    int off[24][3];
+    int ns = big_stencil(off, c->stencil);
+    double A[24 * 9], B[24 * NV], X[9 * NV];
     for (int s = 0; s < ns; ++s) {
         int ii = i + off[s][0], jj = j + off[s][1], kk = k + off[s][2];
         double mn[9];
@@ -547,27 +594,29 @@ static void reconstruct_cell_proj(const orc_cfg *c, const orc_geom *G, const dou
     for (int v = 0; v < NV; ++v)
         for (int m = 0; m < 9; ++m) r->a[v][m] = X[m * NV + v];
 
-    /* P_m, m = 1..24: linear least squares over the 4 neighbours of S_m */
-    int so[24][4][3];
-    sub_stencils(so);
-    for (int s = 0; s < 24; ++s) {
+    /* P_m, m = 1..nsub: linear least squares over the neighbours of S_m
+     * (4 for S, 3 for S', where the system is square) */
+    int so[24][4][3], nrow;
+    const int nsub = sub_stencils_sel(so, &nrow, c->stencil);
+    for (int s = 0; s < nsub; ++s) {
         double As[4 * 3], Bs[4 * NV], Xs[3 * NV];
-        for (int rr = 0; rr < 4; ++rr) {
+        for (int rr = 0; rr < nrow; ++rr) {
             int ii = i + so[s][rr][0], jj = j + so[s][rr][1], kk = k + so[s][rr][2];
             double mn[9];
             cell_monomial_means(BLK(so[s][rr][0], so[s][rr][1], so[s][rr][2]), r->cen, r->h, mn);
             for (int m = 0; m < 3; ++m) As[rr * 3 + m] = mn[m] - r->mean[m];
             for (int v = 0; v < NV; ++v) Bs[rr * NV + v] = data_value(D, Qp, P, v, cid(D, ii, jj, kk)) - r->Qc[v];
         }
-        lsq_householder(4, 3, As, NV, Bs, Xs);
+        lsq_householder(nrow, 3, As, NV, Bs, Xs);
         for (int v = 0; v < NV; ++v)
             for (int m = 0; m < 3; ++m) r->b[s][v][m] = Xs[m * NV + v];
     }
 
-    /* linear weights: gamma_0 = 1 - 24 Gamma, gamma_m = Gamma */
+    /* linear weights: gamma_0 = 1 - nsub Gamma, gamma_m = Gamma (reading for
+     * S': the same Gamma for each of its 8 sub-stencils) */
     double gam[25];
-    gam[0] = 1.0 - 24.0 * c->Gamma_lin;
-    for (int s = 1; s <= 24; ++s) gam[s] = c->Gamma_lin;
+    gam[0] = 1.0 - nsub * c->Gamma_lin;
+    for (int s = 1; s <= nsub; ++s) gam[s] = c->Gamma_lin;
 
     /* multi-indices l with 1 <= |l| <= 2, each counted once (Reading) */
     static const int LIDX[9][3] = {
@@ -577,7 +626,7 @@ static void reconstruct_cell_proj(const orc_cfg *c, const orc_geom *G, const dou
         /* smoothness indicators, eq. (indicator), integrals by the cell's
          * 2x2x2 Gauss rule in physical coordinates */
         double beta[25];
-        for (int s = 0; s <= 24; ++s) {
+        for (int s = 0; s <= nsub; ++s) {
             int nl = (s == 0) ? 9 : 3;
             int nt = (s == 0) ? 9 : 3;
             const double *cf = (s == 0) ? r->a[v] : r->b[s - 1][v];
@@ -599,23 +648,23 @@ static void reconstruct_cell_proj(const orc_cfg *c, const orc_geom *G, const dou
         }
         /* global indicator, eq. (para) */
         double tau = 0.0;
-        for (int s = 1; s <= 24; ++s) tau += fabs(beta[0] - beta[s]) / 24.0;
+        for (int s = 1; s <= nsub; ++s) tau += fabs(beta[0] - beta[s]) / nsub;
         /* nonlinear weights, eq. (nonlinear) */
         double w[25], wsum = 0.0;
-        for (int s = 0; s <= 24; ++s) {
+        for (int s = 0; s <= nsub; ++s) {
             double ratio = tau / (beta[s] + c->weno_eps);
             w[s] = gam[s] * (1.0 + (c->weno_pow == 2 ? ratio * ratio : ratio));
             wsum += w[s];
         }
         double wb[25];
-        for (int s = 0; s <= 24; ++s) wb[s] = w[s] / wsum;
+        for (int s = 0; s <= nsub; ++s) wb[s] = w[s] / wsum;
         for (int s = 0; s <= 24; ++s) {
-            r->beta[v][s] = beta[s];
-            r->wbar[v][s] = wb[s];
+            r->beta[v][s] = s <= nsub ? beta[s] : 0.0;
+            r->wbar[v][s] = s <= nsub ? wb[s] : 0.0;
         }
         /* P~ = wb0 (P0/g0 - sum g_m/g0 P_m) + sum wb_m P_m */
         for (int m = 0; m < 9; ++m) r->coef[v][m] = (wb[0] / gam[0]) * r->a[v][m];
-        for (int s = 1; s <= 24; ++s)
+        for (int s = 1; s <= nsub; ++s)
             for (int m = 0; m < 3; ++m)
                 r->coef[v][m] += (wb[s] - wb[0] * gam[s] / gam[0]) * r->b[s - 1][v][m];
     }
@@ -654,7 +703,7 @@ static void reconstruct_cell_proj(const orc_cfg *c, const orc_geom *G, const dou
     if (c->limiter) {
         double xg[24][3];
         cell_face_gauss_points(G, i, j, k, xg);
-        for (int s = 0; s <= 24 && !r->flag; ++s)
+        for (int s = 0; s <= nsub && !r->flag; ++s)
             for (int g = 0; g < 24 && !r->flag; ++g) {
                 double W[NV];
                 for (int v = 0; v < NV; ++v)
@@ -1352,7 +1401,7 @@ static int residuals(const orc_cfg *c, const orc_geom *G, const double *q, doubl
     unsigned char *need = (unsigned char *)calloc(D->ncell, 1);
     slim_rec *rec = NULL;
     if (!Qp || !slot || !need) { free(Qp); free(slot); free(need); return -1; }
-    fill_ghosts(c, D, q, Qp);
+    if (fill_ghosts(c, D, q, Qp)) { free(Qp); free(slot); free(need); return -1; }
 
     /* which cells must be reconstructed: a requested cell and its 6 face neighbours */
     size_t nout = ncells >= 0 ? (size_t)ncells : nint;
@@ -1514,7 +1563,7 @@ int orc_reconstruct(const orc_cfg *c, const double *q, double t, double *coef, i
     const orc_dims *D = &G.D;
     double *Qp = (double *)malloc(D->ncell * NV * sizeof(double));
     if (!Qp) { geom_free(&G); return -1; }
-    fill_ghosts(c, D, q, Qp);
+    if (fill_ghosts(c, D, q, Qp)) { free(Qp); geom_free(&G); return -1; }
     long nint = (long)c->n[0] * c->n[1] * c->n[2];
 #pragma omp parallel for schedule(dynamic, 64) num_threads(ORC_THREADS(c))
     for (long lin = 0; lin < nint; ++lin) {
@@ -1544,7 +1593,7 @@ int orc_weno_weights(const orc_cfg *c, const double *q, double t, long lin, doub
     const orc_dims *D = &G.D;
     double *Qp = (double *)malloc(D->ncell * NV * sizeof(double));
     if (!Qp) { geom_free(&G); return -1; }
-    fill_ghosts(c, D, q, Qp);
+    if (fill_ghosts(c, D, q, Qp)) { free(Qp); geom_free(&G); return -1; }
     int i = (int)(lin % c->n[0]), j = (int)((lin / c->n[0]) % c->n[1]), k = (int)(lin / ((long)c->n[0] * c->n[1]));
     cell_rec r;
     reconstruct_cell(c, &G, Qp, i, j, k, &r);
@@ -1568,7 +1617,7 @@ int orc_eval_reconstruction(const orc_cfg *c, const double *q, double t, long li
     const orc_dims *D = &G.D;
     double *Qp = (double *)malloc(D->ncell * NV * sizeof(double));
     if (!Qp) { geom_free(&G); return -1; }
-    fill_ghosts(c, D, q, Qp);
+    if (fill_ghosts(c, D, q, Qp)) { free(Qp); geom_free(&G); return -1; }
     int i = (int)(lin % c->n[0]), j = (int)((lin / c->n[0]) % c->n[1]), k = (int)(lin / ((long)c->n[0] * c->n[1]));
     cell_rec r;
     slim_rec sr;
@@ -1711,11 +1760,24 @@ void orc_moment_matrix(const orc_cfg *c, const double *W, double *M)
 }
 
 /* geometry of the big stencil and sub-stencils, for the tests */
+/* the stencil tables of S' (Remark of Sec. 2): big[24][3], sub[8][3][3] */
+void orc_stencils_sprime(int *big, int *sub)
+{
+    int off[24][3], so[24][4][3], nrow;
+    big_stencil(off, 1);
+    for (int s = 0; s < 24; ++s)
+        for (int d = 0; d < 3; ++d) big[s * 3 + d] = off[s][d];
+    int ns = sub_stencils_sel(so, &nrow, 1);
+    for (int m = 0; m < ns; ++m)
+        for (int r = 0; r < 3; ++r)
+            for (int d = 0; d < 3; ++d) sub[(m * 3 + r) * 3 + d] = so[m][r][d];
+}
+
 void orc_stencils(int *big, int *sub)
 {
-    int off[18][3], so[24][4][3];
-    big_stencil(off);
+    int off[24][3], so[24][4][3];
+    big_stencil(off, 0);
     sub_stencils(so);
-    memcpy(big, off, sizeof off);
+    memcpy(big, off, 18 * sizeof off[0]);
     memcpy(sub, so, sizeof so);
 }
