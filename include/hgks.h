@@ -94,7 +94,11 @@ int hgks_create(const hgks_grid_t *grid, double gamma, double mu, double Pr, con
  * "mu_T_ref" (viscosity law mu (T/T_ref)^mu_power of the isotropic
  * turbulence of Sec. 4, 0.76 there, evaluated at the temperature p/rho of
  * the interface equilibrium state in the collision time; mu_power = 0, the
- * default, keeps mu constant), "characteristic" (1/0: reconstruct the
+ * default, keeps mu constant), "stencil" (0: the big stencil S with its
+ * 24 sub-stencils; 1: S' of the Remark of Sec. 2, S plus the six axis cells
+ * two steps away, with the 8 octant sub-stencils and gamma_0 = 1 - 8 Gamma;
+ * uniform mesh and conservative variables only), "characteristic" (1/0:
+ * reconstruct the
  * characteristic variables L Q of
  * Sec. 4, L the inverse of the right eigenvectors of the Euler flux
  * Jacobian along the face normal at the mean of the face's two cell

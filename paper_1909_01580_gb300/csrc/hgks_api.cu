@@ -167,7 +167,8 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
     *out = nullptr;
     for (int d = 0; d < 3; ++d) {
         // two ghost layers mirror or wrap at most two interior cells
-        if (grid->n[d] < 2 || !(grid->hi[d] > grid->lo[d]))
+        if (grid->n[d] < 2 || !(grid->hi[d] > grid->lo[d]) ||
+            (grid->n[d] < hk::GHOST && (bc[2 * d] == HGKS_BC_REFLECTIVE || bc[2 * d + 1] == HGKS_BC_REFLECTIVE)))
             return fail(nullptr, HGKS_E_INVALID, "each axis needs at least 2 cells and hi > lo%s");
     }
     if (grid->mesh < 0 || grid->mesh > 2)
@@ -207,9 +208,9 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
     g.nx = grid->n[0];
     g.ny = grid->n[1];
     g.nz = grid->n[2];
-    g.px = g.nx + 4;
-    g.py = g.ny + 4;
-    g.pz = g.nz + 4;
+    g.px = g.nx + 2 * hk::GHOST;
+    g.py = g.ny + 2 * hk::GHOST;
+    g.pz = g.nz + 2 * hk::GHOST;
     g.cx = g.nx + 2;
     g.cy = g.ny + 2;
     g.cz = g.nz + 2;
@@ -263,12 +264,12 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
     }
     if (mapped && ok) {
         // the map x = xi + amp S(t) prod sin(2 pi (xi - lo)/L): sine factors
-        // at vertex indices -2..n+2 of each axis
-        const int nv[3] = {g.nx + 5, g.ny + 5, g.nz + 5};
+        // at vertex indices -GHOST..n+GHOST of each axis
+        const int nv[3] = {g.nx + 2 * hk::GHOST + 1, g.ny + 2 * hk::GHOST + 1, g.nz + 2 * hk::GHOST + 1};
         std::vector<double> tab(nv[0] + nv[1] + nv[2]);
         size_t o = 0;
         for (int d = 0; d < 3; ++d)
-            for (int iv = -2; iv <= grid->n[d] + 2; ++iv, ++o) {
+            for (int iv = -hk::GHOST; iv <= grid->n[d] + hk::GHOST; ++iv, ++o) {
                 const double xi = grid->lo[d] + (grid->hi[d] - grid->lo[d]) * (double)iv / (double)grid->n[d];
                 tab[o] = sin(2.0 * M_PI * (xi - grid->lo[d]) / (grid->hi[d] - grid->lo[d]));
             }
@@ -343,10 +344,18 @@ extern "C" int hgks_set_option(hgks_t *h, const char *key, double value)
     } else if (!strcmp(key, "mu_T_ref")) {
         if (!(value > 0.0)) return fail(h, HGKS_E_INVALID, "mu_T_ref must be > 0%s");
         h->S.T_ref = value;
+    } else if (!strcmp(key, "stencil")) {
+        // 0: the big stencil S with 24 sub-stencils; 1: S' with 8 (Remark of Sec. 2)
+        if (value != 0.0 && value != 1.0) return fail(h, HGKS_E_INVALID, "stencil must be 0 (S) or 1 (S')%s");
+        if (value == 1.0 && (h->mesh != 0 || h->charvar))
+            return fail(h, HGKS_E_INVALID, "the stencil S' needs the uniform mesh and conservative variables%s");
+        h->S.sprime = value == 1.0;
     } else if (!strcmp(key, "characteristic")) {
         if (value != 0.0 && value != 1.0) return fail(h, HGKS_E_INVALID, "characteristic must be 0 or 1%s");
         if (value == 1.0 && h->mesh != 0)
             return fail(h, HGKS_E_INVALID, "characteristic variables need the uniform mesh%s");
+        if (value == 1.0 && h->S.sprime)
+            return fail(h, HGKS_E_INVALID, "characteristic variables use the stencil S%s");
         if (value == 1.0 && !h->coefc[0]) {
             const Geo &g = h->g;
             const size_t elem = h->precision == HGKS_MIXED ? sizeof(float) : sizeof(double);

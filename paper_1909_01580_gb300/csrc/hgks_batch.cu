@@ -219,8 +219,11 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 static int validate_grid(const hgks_grid_t *grid, double gamma, double mu, double Pr, const int bc[6], double *hx_out)
 {
     if (!grid || !bc) return HGKS_E_INVALID;
-    for (int d = 0; d < 3; ++d)
+    for (int d = 0; d < 3; ++d) {
         if (grid->n[d] < 2 || !(grid->hi[d] > grid->lo[d])) return HGKS_E_INVALID;
+        if (grid->n[d] < hk::GHOST && (bc[2 * d] == HGKS_BC_REFLECTIVE || bc[2 * d + 1] == HGKS_BC_REFLECTIVE))
+            return HGKS_E_INVALID;
+    }
     if (grid->mesh != 0 || grid->mesh_amp != 0.0 || grid->mesh_omega != 0.0) return HGKS_E_INVALID;
     const double hx = (grid->hi[0] - grid->lo[0]) / grid->n[0];
     for (int d = 1; d < 3; ++d) {
@@ -244,9 +247,9 @@ static Geo make_geo(const hgks_grid_t *grid, double hx, const int bc[6])
     g.nx = grid->n[0];
     g.ny = grid->n[1];
     g.nz = grid->n[2];
-    g.px = g.nx + 4;
-    g.py = g.ny + 4;
-    g.pz = g.nz + 4;
+    g.px = g.nx + 2 * hk::GHOST;
+    g.py = g.ny + 2 * hk::GHOST;
+    g.pz = g.nz + 2 * hk::GHOST;
     g.cx = g.nx + 2;
     g.cy = g.ny + 2;
     g.cz = g.nz + 2;

@@ -61,6 +61,7 @@ struct Scheme {
     double Gamma_lin;  // linear weight of each sub-stencil
     int weno_pow;      // exponent on tau/(beta + eps)
     int limiter;       // positivity fallback on/off
+    int sprime = 0;       // 1: big stencil S' with 8 sub-stencils (Remark of Sec. 2)
     double mu_pow = 0.0;  // viscosity law mu (T/T_ref)^mu_pow (0: constant mu)
     double T_ref = 1.0;   // reference temperature p/rho of that law
     int viscous;       // mu > 0
@@ -103,8 +104,11 @@ template <typename R> HK_HD FluxK<R> fluxk(const Scheme &S)
 template <> HK_HD FluxK<double> fluxk<double>(const Scheme &S) { return S.kd; }
 template <> HK_HD FluxK<float> fluxk<float>(const Scheme &S) { return S.kf; }
 
-// Mesh: a uniform grid of cubes with GH = 2 ghost layers in the state
-// arrays and one ghost layer in the reconstruction arrays.
+// Mesh: a uniform grid of cubes with GHOST = 3 ghost layers in the state
+// arrays (the reconstruction of the ghost ring reaches two cells further
+// with the big stencil S' of Sec. 2) and one ghost layer in the
+// reconstruction arrays.
+constexpr int GHOST = 3;
 struct Geo {
     int nx, ny, nz;          // interior cells
     int px, py, pz;          // padded state extents (n + 4)
@@ -118,7 +122,7 @@ struct Geo {
 
 HK_HD long long pidx(const Geo &g, int i, int j, int k)
 {
-    return ((long long)(k + 2) * g.py + (j + 2)) * g.px + (i + 2);
+    return ((long long)(k + GHOST) * g.py + (j + GHOST)) * g.px + (i + GHOST);
 }
 HK_HD long long cidx(const Geo &g, int i, int j, int k)
 {
@@ -565,6 +569,7 @@ template <typename R> struct Stencil {
     // neighbours e[plane][sa][sb] for planes (x,y), (y,z), (z,x)
     R f[3][2];
     R e[3][2][2];
+    R f2[3][2];  // S' only: the axis cells two steps away (-/+)
 };
 
 template <typename R> HK_HD void big_stencil_P0(const Stencil<R> &st, R a[9])
@@ -677,6 +682,71 @@ template <typename R> HK_HD void poly_value_grad(const R c[9], const R X[3], R i
     grad[2] = (c[2] + R(2) * c[5] * X[2] + c[7] * X[0] + c[8] * X[1]) * ih;
 }
 
+// ---------------------------------------------------------------------------
+// The alternative stencil S' (Remark of Sec. 2): S plus the six axis cells
+// two steps away, and 8 sub-stencils {c, s_x e_x, s_y e_y, s_z e_z}, one per
+// octant.  On cubes the normal matrix of P0 over S' is diag(18 I_3,
+// 38 I_3 + 4 11^T, 4 I_3), so
+//   a_d  = (1/18) sum o_d dQ,   a_de = (1/4) sum o_d o_e dQ,
+//   a_dd = (s_dd - (2/25) sum_e s_ee)/38,   s_dd = sum o_d^2 dQ,
+// and each octant sub-stencil is square: b_d = s_d dQ(s_d e_d).
+// ---------------------------------------------------------------------------
+template <typename R> HK_HD void big_stencil_P0_sp(const Stencil<R> &st, R a[9])
+{
+    R sd[3], sdd[3], sde[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int p1 = d, p2 = (d + 2) % 3;
+        R lin = st.f[d][1] - st.f[d][0] + R(2) * (st.f2[d][1] - st.f2[d][0]);
+        R quad = st.f[d][1] + st.f[d][0] + R(4) * (st.f2[d][1] + st.f2[d][0]);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            lin += st.e[p1][1][s] - st.e[p1][0][s];
+            quad += st.e[p1][1][s] + st.e[p1][0][s];
+            lin += st.e[p2][s][1] - st.e[p2][s][0];
+            quad += st.e[p2][s][1] + st.e[p2][s][0];
+        }
+        sd[d] = lin;
+        sdd[d] = quad;
+        sde[d] = st.e[d][1][1] + st.e[d][0][0] - st.e[d][1][0] - st.e[d][0][1];
+    }
+    const R tr = sdd[0] + sdd[1] + sdd[2];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        a[d] = sd[d] * R(1.0 / 18.0);
+        a[3 + d] = (sdd[d] - R(2.0 / 25.0) * tr) * R(1.0 / 38.0);
+    }
+    a[6] = R(0.25) * sde[0];
+    a[7] = R(0.25) * sde[2];
+    a[8] = R(0.25) * sde[1];
+}
+
+// octant sub-stencil M of S', signs in the printed order (+++), (-++), (+-+),
+// (--+), (++-), (-+-), (+--), (---)
+template <int M, typename R> HK_HD void sub_stencil_sp(const Stencil<R> &st, R b[3])
+{
+    constexpr int sx = (M & 1) ? 0 : 1, sy = (M & 2) ? 0 : 1, sz = (M & 4) ? 0 : 1;
+    b[0] = sx ? st.f[0][1] : -st.f[0][0];
+    b[1] = sy ? st.f[1][1] : -st.f[1][0];
+    b[2] = sz ? st.f[2][1] : -st.f[2][0];
+}
+
+#define HK_FOR_SUBSTENCILS_SP(X) X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7)
+
+template <typename R> HK_HD void sub_stencil_sp_rt(const Stencil<R> &st, int m, R b[3])
+{
+    switch (m) {
+#define HK_CASE_SP(M)                   \
+    case M:                             \
+        sub_stencil_sp<M, R>(st, b);    \
+        break;
+        HK_FOR_SUBSTENCILS_SP(HK_CASE_SP)
+#undef HK_CASE_SP
+    default:
+        b[0] = b[1] = b[2] = R(0);
+    }
+}
+
 // WENO-AO combination for one conserved variable (Sec. 2): P0, the 24
 // linear P_m, their indicators, tau of eq. (para), the nonlinear weights of
 // eq. (nonlinear) and P~ = (w0/g0) P0 + sum (w_m - w0 g_m/g0) P_m, returned
@@ -725,6 +795,56 @@ HK_HD void weno_ao(const Stencil<R> &st, const Scheme &S, R out[9], R &rad)
     }
     HK_FOR_SUBSTENCILS(HK_PASS2)
 #undef HK_PASS2
+    const R iw = R(1) / wsum;
+    const R f0 = w0 * ig0;
+#pragma unroll
+    for (int n = 0; n < 9; ++n) out[n] = iw * (f0 * a[n] + (n < 3 ? lin[n] : R(0)));
+}
+
+// WENO-AO with S' and its 8 sub-stencils: linear weights gamma_0 = 1 - 8
+// Gamma, gamma_m = Gamma (reading), tau the mean of |beta_0 - beta_m| over
+// the 8; otherwise as weno_ao
+template <typename R>
+HK_HD void weno_ao_sp(const Stencil<R> &st, const Scheme &S, R out[9], R &rad)
+{
+    const R g0 = R(1.0 - 8.0 * S.Gamma_lin), gm = R(S.Gamma_lin), eps = R(S.weno_eps);
+    const R ig0 = R(1) / g0;
+    R a[9];
+    big_stencil_P0_sp(st, a);
+    const R beta0 = beta_quadratic(a);
+    R r = bound_quadratic(a);
+    R tau = R(0);
+#define HK_PASS1_SP(M)                                                \
+    {                                                                 \
+        R b[3];                                                       \
+        sub_stencil_sp<M>(st, b);                                     \
+        const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];         \
+        tau += m_abs(beta0 - bm);                                     \
+        r = m_max(r, bound_linear(b));                                \
+    }
+    HK_FOR_SUBSTENCILS_SP(HK_PASS1_SP)
+#undef HK_PASS1_SP
+    tau *= R(1.0 / 8.0);
+    rad = r;
+    const R x0 = tau / (beta0 + eps);
+    const R w0 = g0 * (R(1) + (S.weno_pow == 2 ? x0 * x0 : x0));
+    R wsum = w0;
+    R lin[3] = {R(0), R(0), R(0)};
+#define HK_PASS2_SP(M)                                                \
+    {                                                                 \
+        R b[3];                                                       \
+        sub_stencil_sp<M>(st, b);                                     \
+        const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];         \
+        const R xm = tau / (bm + eps);                                \
+        const R wm = gm * (R(1) + (S.weno_pow == 2 ? xm * xm : xm));  \
+        wsum += wm;                                                   \
+        const R cm = wm - w0 * gm * ig0;                              \
+        lin[0] += cm * b[0];                                          \
+        lin[1] += cm * b[1];                                          \
+        lin[2] += cm * b[2];                                          \
+    }
+    HK_FOR_SUBSTENCILS_SP(HK_PASS2_SP)
+#undef HK_PASS2_SP
     const R iw = R(1) / wsum;
     const R f0 = w0 * ig0;
 #pragma unroll

@@ -22,7 +22,7 @@ __device__ __forceinline__ void halo_item(double *__restrict__ Q, const Geo &g, 
 {
     if (t >= g.pstride) return;
     const int ip = (int)(t % g.px), jp = (int)((t / g.px) % g.py), kp = (int)(t / ((long long)g.px * g.py));
-    const int idx[3] = {ip - 2, jp - 2, kp - 2};
+    const int idx[3] = {ip - GHOST, jp - GHOST, kp - GHOST};
     const int n[3] = {g.nx, g.ny, g.nz};
     int src[3];
     int flip[3] = {0, 0, 0};
@@ -30,14 +30,16 @@ __device__ __forceinline__ void halo_item(double *__restrict__ Q, const Geo &g, 
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         int s = idx[d];
+        // periodic wraps modulo n (the ghost layers may be deeper than the
+        // grid); reflective needs n >= GHOST (checked at creation)
         if (s < 0) {
             ghost = true;
-            if (g.bc[2 * d] == 0) s += n[d];
+            if (g.bc[2 * d] == 0) s = ((s % n[d]) + n[d]) % n[d];
             else if (g.bc[2 * d] == 2) s = 0;
             else { s = -1 - s; flip[d] = 1; }
         } else if (s >= n[d]) {
             ghost = true;
-            if (g.bc[2 * d + 1] == 0) s -= n[d];
+            if (g.bc[2 * d + 1] == 0) s = s % n[d];
             else if (g.bc[2 * d + 1] == 2) s = n[d] - 1;
             else { s = 2 * n[d] - 1 - s; flip[d] = 1; }
         }
@@ -73,6 +75,20 @@ __device__ __forceinline__ void load_stencil(const double *__restrict__ Qv, cons
         for (int sa = 0; sa < 2; ++sa)
 #pragma unroll
             for (int sb = 0; sb < 2; ++sb) st.e[p][sa][sb] = R(Qv[c + (sa ? a : -a) + (sb ? b : -b)] - qc);
+    }
+}
+
+// the six axis cells two steps away, for S' (formed in FP64 like the rest)
+template <typename R>
+__device__ __forceinline__ void load_stencil_far(const double *__restrict__ Qv, const Geo &g, int i, int j, int k,
+                                                 double qc, Stencil<R> &st)
+{
+    const long long sd[3] = {1, g.px, (long long)g.px * g.py};
+    const long long c = pidx(g, i, j, k);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        st.f2[d][0] = R(Qv[c - 2 * sd[d]] - qc);
+        st.f2[d][1] = R(Qv[c + 2 * sd[d]] - qc);
     }
 }
 
@@ -115,6 +131,45 @@ __device__ __noinline__ bool positivity_violated(const double *__restrict__ Q, c
     return false;
 }
 
+// the same literal check with S' and its 8 sub-stencils
+template <typename R>
+__device__ __noinline__ bool positivity_violated_sp(const double *__restrict__ Q, const Geo &g, int i, int j, int k,
+                                                    R gamma)
+{
+    R qcv[5];
+    Stencil<R> st[5];
+    for (int v = 0; v < 5; ++v) {
+        const double qc = Q[v * g.pstride + pidx(g, i, j, k)];
+        qcv[v] = R(qc);
+        load_stencil(Q + v * g.pstride, g, i, j, k, qc, st[v]);
+        load_stencil_far(Q + v * g.pstride, g, i, j, k, qc, st[v]);
+    }
+    for (int m = 0; m <= 8; ++m) {
+        R cf[5][9];
+        for (int v = 0; v < 5; ++v) {
+            if (m == 0) {
+                big_stencil_P0_sp(st[v], cf[v]);
+            } else {
+                R b[3];
+                sub_stencil_sp_rt(st[v], m - 1, b);
+                for (int n = 0; n < 9; ++n) cf[v][n] = n < 3 ? b[n] : R(0);
+            }
+        }
+        for (int gq = 0; gq < 24; ++gq) {
+            const int d = gq / 8, side = (gq / 4) & 1, ga = (gq >> 1) & 1, gb = gq & 1;
+            R X[3];
+            X[d] = side ? R(0.5) : R(-0.5);
+            X[(d + 1) % 3] = ga ? R(GAUSS_S) : R(-GAUSS_S);
+            X[(d + 2) % 3] = gb ? R(GAUSS_S) : R(-GAUSS_S);
+            R W[5];
+            for (int v = 0; v < 5; ++v) W[v] = qcv[v] + poly9(cf[v], X);
+            const R p = (gamma - R(1)) * (W[4] - R(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / W[0]);
+            if (W[0] < R(0) || p < R(0)) return true;
+        }
+    }
+    return false;
+}
+
 // WENO-AO reconstruction (Sec. 2) of one cell of the (n+2)^3 box, t its
 // linear index there; writes Q_c and the 9 coefficients of P~ - Q_c per
 // variable, and the positivity flag
@@ -134,7 +189,12 @@ __device__ __forceinline__ void recon_item(const double *__restrict__ Q, R *__re
         Stencil<R> st;
         load_stencil(Qv, g, i, j, k, qc, st);
         R out[9];
-        weno_ao(st, S, out, rad[v]);
+        if (S.sprime) {
+            load_stencil_far(Qv, g, i, j, k, qc, st);
+            weno_ao_sp(st, S, out, rad[v]);
+        } else {
+            weno_ao(st, S, out, rad[v]);
+        }
         coef[coef_slot(v, 0) * g.cstride + t] = R(qc);
 #pragma unroll
         for (int n = 0; n < 9; ++n) coef[coef_slot(v, 1 + n) * g.cstride + t] = out[n];
@@ -143,7 +203,8 @@ __device__ __forceinline__ void recon_item(const double *__restrict__ Q, R *__re
     // check of all 25 polynomials at the 24 Gauss points only when it fails
     bool bad = false;
     if (S.limiter && !positivity_certain(qcv, rad, fluxk<R>(S).gamma))
-        bad = positivity_violated<R>(Q, g, i, j, k, fluxk<R>(S).gamma);
+        bad = S.sprime ? positivity_violated_sp<R>(Q, g, i, j, k, fluxk<R>(S).gamma)
+                       : positivity_violated<R>(Q, g, i, j, k, fluxk<R>(S).gamma);
     if (bad) {
         for (int v = 0; v < 5; ++v)
             for (int n = 1; n < 10; ++n) coef[coef_slot(v, n) * g.cstride + t] = R(0);

@@ -15,7 +15,8 @@ __global__ void __launch_bounds__(128) k_geom(double *__restrict__ geo, Geo g, M
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.pstride) return;
-    const int i = (int)(t % g.px) - 2, j = (int)((t / g.px) % g.py) - 2, k = (int)(t / ((long long)g.px * g.py)) - 2;
+    const int i = (int)(t % g.px) - GHOST, j = (int)((t / g.px) % g.py) - GHOST,
+              k = (int)(t / ((long long)g.px * g.py)) - GHOST;
     const double ts = ctl ? stage_time(ctl, half) : t_fixed;
     const double Sf = map_factor(m, ts);
     if (ctl && t == 0) {

@@ -9,7 +9,8 @@ namespace hk {
 
 // The mesh map: x_d = xi_d + amp S(t) prod_e sin(2 pi (xi_e - lo_e)/L_e)
 // with S = 1 (static) or sin(omega t) (moving); xi on a uniform reference
-// grid.  sx/sy/sz hold the sine factor at vertex indices -2..n+2 (offset 2).
+// grid.  sx/sy/sz hold the sine factor at vertex indices -GHOST..n+GHOST
+// (offset GHOST).
 struct MapGeo {
     double lo[3], hi[3];
     int n[3];
@@ -32,7 +33,7 @@ HK_HD double map_factor(const MapGeo &m, double t) { return m.moving ? sin(m.ome
 HK_HD void vertex_pos(const MapGeo &m, int i, int j, int k, double S, double x[3])
 {
     const int idx[3] = {i, j, k};
-    const double s = m.sx[i + 2] * m.sy[j + 2] * m.sz[k + 2];
+    const double s = m.sx[i + GHOST] * m.sy[j + GHOST] * m.sz[k + GHOST];
     const double disp = m.amp * S * s;
 #pragma unroll
     for (int d = 0; d < 3; ++d) x[d] = (m.lo[d] + (m.hi[d] - m.lo[d]) * (double)idx[d] / (double)m.n[d]) + disp;
@@ -41,7 +42,7 @@ HK_HD void vertex_pos(const MapGeo &m, int i, int j, int k, double S, double x[3
 // vertex velocity: amp omega cos(omega t) times the sine factor (moving mesh)
 HK_HD void vertex_vel(const MapGeo &m, int i, int j, int k, double C, double v[3])
 {
-    const double s = m.sx[i + 2] * m.sy[j + 2] * m.sz[k + 2];
+    const double s = m.sx[i + GHOST] * m.sy[j + GHOST] * m.sz[k + GHOST];
     const double vel = m.moving ? m.amp * m.omega * C * s : 0.0;
     v[0] = v[1] = v[2] = vel;
 }
@@ -67,7 +68,7 @@ HK_HD void cell_geometry(const MapGeo &m, int i, int j, int k, double S, double 
     double sv[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-        sv[q] = m.sx[i + (q & 1) + 2] * m.sy[j + ((q >> 1) & 1) + 2] * m.sz[k + (q >> 2) + 2];
+        sv[q] = m.sx[i + (q & 1) + GHOST] * m.sy[j + ((q >> 1) & 1) + GHOST] * m.sz[k + (q >> 2) + GHOST];
     const double hprod = h[0] * h[1] * h[2];
     double Y[8][3], w[8], vol = 0.0, m1[3] = {0, 0, 0};
 #pragma unroll
@@ -744,7 +745,7 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
         R sv[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-            sv[q] = R(m.sx[i + (q & 1) + 2]) * R(m.sy[j + ((q >> 1) & 1) + 2]) * R(m.sz[k + (q >> 2) + 2]);
+            sv[q] = R(m.sx[i + (q & 1) + GHOST]) * R(m.sy[j + ((q >> 1) & 1) + GHOST]) * R(m.sz[k + (q >> 2) + GHOST]);
         const int idx[3] = {i, j, k};
         R x0[3], hr[3];
 #pragma unroll
@@ -905,7 +906,7 @@ __device__ __forceinline__ void flux_mapped_item(const R *__restrict__ coef, dou
             int o[3] = {i, j, k};
             o[A] += sa;
             o[B] += sb;
-            const R sv = R(m.sx[o[0] + 2]) * R(m.sy[o[1] + 2]) * R(m.sz[o[2] + 2]);
+            const R sv = R(m.sx[o[0] + GHOST]) * R(m.sy[o[1] + GHOST]) * R(m.sz[o[2] + GHOST]);
             const R qa = R(2 * sa - 1), qb = R(2 * sb - 1);
             sphi += R(0.25) * (R(1) + R(2) * qa * ea) * (R(1) + R(2) * qb * eb) * sv;
             spa += R(0.5) * qa * (R(1) + R(2) * qb * eb) * sv;

@@ -71,7 +71,8 @@ extern "C" int hgks_flux_noalloc(const hgks_grid_t *grid, double gamma, double m
         return HGKS_E_INVALID;
     }
     for (int d = 0; d < 3; ++d) {
-        if (grid->n[d] < 2 || !(grid->hi[d] > grid->lo[d])) {
+        if (grid->n[d] < 2 || !(grid->hi[d] > grid->lo[d]) ||
+            (grid->n[d] < hk::GHOST && (bc[2 * d] == HGKS_BC_REFLECTIVE || bc[2 * d + 1] == HGKS_BC_REFLECTIVE))) {
             hgks_internal_set_error("hgks_flux_noalloc: each axis needs at least 2 cells and hi > lo");
             return HGKS_E_INVALID;
         }
@@ -108,9 +109,9 @@ extern "C" int hgks_flux_noalloc(const hgks_grid_t *grid, double gamma, double m
     g.nx = grid->n[0];
     g.ny = grid->n[1];
     g.nz = grid->n[2];
-    g.px = g.nx + 4;
-    g.py = g.ny + 4;
-    g.pz = g.nz + 4;
+    g.px = g.nx + 2 * hk::GHOST;
+    g.py = g.ny + 2 * hk::GHOST;
+    g.pz = g.nz + 2 * hk::GHOST;
     g.cx = g.nx + 2;
     g.cy = g.ny + 2;
     g.cz = g.nz + 2;
