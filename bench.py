@@ -259,6 +259,55 @@ def moving_run(steps, warmup, n=96):
     return out
 
 
+def workload_run(name, q0, lo, hi, steps, warmup, solver_kw=None, options=None):
+    """Cell-stage updates/s of one workload on one handle per precision
+    (CFL 0.35, CUDA events on the handle's stream), with the per-phase split."""
+    import torch
+    from paper_1909_01580_gb300 import hgks
+    n = q0.shape[1:][::-1]
+    out = {"workload": name}
+    for pname, prec in (("fp64", hgks.HGKS_FP64), ("mixed", hgks.HGKS_MIXED)):
+        stream = torch.cuda.Stream()
+        s = hgks.Solver(n, lo, hi, precision=prec, stream=stream.cuda_stream, **(solver_kw or {}))
+        for k, v in (options or {}).items():
+            hgks.hgks_set_option(s.h, k, v)
+        s.set_state(q0, t=0.0)
+        s.step(warmup, cfl=0.35)
+        hgks.hgks_set_timing(s.h, 1)
+        torch.cuda.synchronize()
+        l0 = s.launches
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        s.step(steps, cfl=0.35, sync=False)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        timing = hgks.hgks_get_timing(s.h)
+        cells = int(np.prod(n))
+        out[pname] = {"value": cells * 2 * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+                      "steps": steps, "launches": s.launches - l0,
+                      "phase_ms_per_step": {k: round(v[0] / steps, 4) for k, v in timing.items()}}
+        s.close()
+        del stream
+    return out
+
+
+def octant_run(steps, warmup, n=128):
+    from paper_1909_01580_gb300 import workloads
+    q0 = workloads.octant_riemann((n, n, n), seed=0)
+    return workload_run(f"octant Riemann problem {n}^3 on [0,1]^3, reflective walls, seed 0, CFL 0.35", q0,
+                        (0, 0, 0), (1, 1, 1), steps, warmup, solver_kw={"bc": (1,) * 6})
+
+
+def turbulence_run(steps, warmup, n=128, mach=0.5):
+    from paper_1909_01580_gb300 import workloads
+    q0, lo, hi, P = workloads.isotropic_turbulence(n, mach, seed=0)
+    return workload_run(f"compressible isotropic turbulence {n}^3, Ma_t {mach}, Re_lambda 72, mu ~ T^0.76, Pr 0.7",
+                        q0, lo, hi, steps, warmup, solver_kw={"mu": P.mu0, "Pr": 0.7},
+                        options={"mu_power": 0.76, "mu_T_ref": P.T0})
+
+
 def serving_run(count=16, sizes=(24, 32, 48), steps=(20, 40), seed=0, load=1.25, precisions=("fp64", "mixed"),
                 arena_gb=4.0):
     """Serving workload: seeded requests (density advection / TGV 50:50,
@@ -362,6 +411,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the small serving run of the default line")
     ap.add_argument("--no-moving", action="store_true", help="skip the 96^3 moving-mesh run of the default line")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the octant-Riemann and isotropic-turbulence runs of the default line")
     ap.add_argument("--serving", action="store_true",
                     help="only the serving benchmark: 64 requests on 24^3..96^3, printed as its own line")
     ap.add_argument("--serving-steps-max", type=int, default=80)
@@ -421,6 +472,9 @@ def main():
             line["mixed"]["e2e"] = res["mixed"].get("e2e")
         if not args.no_moving and world == 1:
             line["moving_mesh"] = moving_run(steps=max(1, min(args.steps, 5)), warmup=2)
+        if not args.no_workloads and world == 1:
+            line["octant_riemann"] = octant_run(steps=max(1, min(args.steps, 5)), warmup=2)
+            line["isotropic_turbulence"] = turbulence_run(steps=max(1, min(args.steps, 5)), warmup=2)
         if not args.no_serving and world == 1:
             line["serving"] = serving_run()
         if not args.no_cpu_baseline and world == 1:

@@ -499,7 +499,7 @@ static int stage_fluxes(hgks_t *h, double *Q, int half = 0, bool geom_ready = fa
     if (h->precision == HGKS_MIXED) {
         float *c = (float *)h->coef;
         {
-            PhaseTimer t(h, HGKS_PHASE_RECON, 1);
+            PhaseTimer t(h, HGKS_PHASE_RECON, 2);
             hk::launch_recon<float>(Q, c, h->flag, g, h->S, h->ctl, s);
         }
         PhaseTimer t(h, HGKS_PHASE_FLUX, 3);
@@ -507,13 +507,14 @@ static int stage_fluxes(hgks_t *h, double *Q, int half = 0, bool geom_ready = fa
     } else {
         double *c = (double *)h->coef;
         {
-            PhaseTimer t(h, HGKS_PHASE_RECON, 1);
+            PhaseTimer t(h, HGKS_PHASE_RECON, 2);
             hk::launch_recon<double>(Q, c, h->flag, g, h->S, h->ctl, s);
         }
         PhaseTimer t(h, HGKS_PHASE_FLUX, 3);
         for (int d = 0; d < 3; ++d) hk::launch_flux<double>(d, c, h->F[d], g, h->S, h->ctl, s);
     }
-    return check_launch(h, 5);
+    // halo, reconstruction and its positivity pass, three face sweeps
+    return check_launch(h, 6);
 }
 
 extern "C" int hgks_step(hgks_t *h, int nsteps, double cfl, double dt_fixed, double t_end, double *t_out,
@@ -651,7 +652,7 @@ extern "C" int hgks_reconstruct(hgks_t *h, double *coef, int *flag)
     hk::launch_set_ctl(h->ctl, h->ctl_host->t, 0.0, 0, s);
     // reconstruction, export and control reset; on a mapped mesh also the
     // geometry and the positivity pass
-    rc = check_launch(h, 3 + (h->mesh != 0 ? 2 : 0));
+    rc = check_launch(h, 4 + (h->mesh != 0 ? 1 : 0));
     if (!rc) {
         cudaMemcpyAsync(coef, dc, 45 * g.ncell * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (flag) cudaMemcpyAsync(flag, df, g.ncell * sizeof(int), cudaMemcpyDeviceToHost, s);

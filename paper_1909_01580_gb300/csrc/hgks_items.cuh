@@ -173,7 +173,10 @@ __device__ __noinline__ bool positivity_violated_sp(const double *__restrict__ Q
 // WENO-AO reconstruction (Sec. 2) of one cell of the (n+2)^3 box, t its
 // linear index there; writes Q_c and the 9 coefficients of P~ - Q_c per
 // variable, and the positivity flag
-template <typename R>
+// SPLIT: leave the literal positivity check to positivity_item (a kernel of
+// its own, whose register demand then does not weigh on this one) and mark
+// the cells whose bound is inconclusive with flag 2
+template <typename R, bool SPLIT = false>
 __device__ __forceinline__ void recon_item(const double *__restrict__ Q, R *__restrict__ coef,
                                            unsigned char *__restrict__ flag, const Geo &g, const Scheme &S, Ctl *ctl,
                                            long long t)
@@ -201,6 +204,10 @@ __device__ __forceinline__ void recon_item(const double *__restrict__ Q, R *__re
     }
     // positivity fallback: the cheap sufficient test first, the literal
     // check of all 25 polynomials at the 24 Gauss points only when it fails
+    if (SPLIT) {
+        flag[t] = (S.limiter && !positivity_certain(qcv, rad, fluxk<R>(S).gamma)) ? 2 : 0;
+        return;
+    }
     bool bad = false;
     if (S.limiter && !positivity_certain(qcv, rad, fluxk<R>(S).gamma))
         bad = S.sprime ? positivity_violated_sp<R>(Q, g, i, j, k, fluxk<R>(S).gamma)
@@ -211,6 +218,82 @@ __device__ __forceinline__ void recon_item(const double *__restrict__ Q, R *__re
         atomicAdd(&ctl->flagged, 1);
     }
     flag[t] = bad ? 1 : 0;
+}
+
+// the literal positivity check (Sec. 4) of the cells marked 2 by
+// recon_item<R, true>, one warp per cell: the warp takes its marked cells in
+// turn, lane m builds polynomial m (P0 for m = 0, the linear P_m after; 25
+// for S, 9 for S') from the cell's stencil and evaluates rho and p at the
+// cell's 24 face Gauss points, and a vote gives the verdict; a violation
+// sets P~ to the cell average.  Every lane of the warp must call this.
+template <typename R>
+__device__ __forceinline__ void positivity_item(const double *__restrict__ Q, R *__restrict__ coef,
+                                                unsigned char *__restrict__ flag, const Geo &g, const Scheme &S,
+                                                Ctl *ctl, long long t)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool mine = t < g.cstride && flag[t] == 2;
+    unsigned pending = __ballot_sync(FULL, mine);
+    const int npoly = S.sprime ? 9 : 25;
+    const R gamma = fluxk<R>(S).gamma;
+    while (pending) {
+        const int owner = __ffs(pending) - 1;
+        pending &= pending - 1;
+        const long long tc = __shfl_sync(FULL, t, owner);
+        const int i = (int)(tc % g.cx) - 1, j = (int)((tc / g.cx) % g.cy) - 1, k = (int)(tc / ((long long)g.cx * g.cy)) - 1;
+        bool bad = false;
+        if (lane < npoly) {
+            R cf[5][9], qcv[5];
+#pragma unroll 1
+            for (int v = 0; v < 5; ++v) {
+                const double *Qv = Q + v * g.pstride;
+                const double qc = Qv[pidx(g, i, j, k)];
+                qcv[v] = R(qc);
+                Stencil<R> st;
+                load_stencil(Qv, g, i, j, k, qc, st);
+                R c9[9];
+                if (lane == 0) {
+                    if (S.sprime) {
+                        load_stencil_far(Qv, g, i, j, k, qc, st);
+                        big_stencil_P0_sp(st, c9);
+                    } else {
+                        big_stencil_P0(st, c9);
+                    }
+                } else {
+                    R b[3];
+                    if (S.sprime) sub_stencil_sp_rt(st, lane - 1, b);
+                    else sub_stencil_rt(st, lane - 1, b);
+#pragma unroll
+                    for (int n = 0; n < 9; ++n) c9[n] = n < 3 ? b[n] : R(0);
+                }
+#pragma unroll
+                for (int n = 0; n < 9; ++n) cf[v][n] = c9[n];
+            }
+#pragma unroll 1
+            for (int gq = 0; gq < 24; ++gq) {
+                const int d = gq / 8, side = (gq / 4) & 1, ga = (gq >> 1) & 1, gb = gq & 1;
+                R X[3];
+                X[d] = side ? R(0.5) : R(-0.5);
+                X[(d + 1) % 3] = ga ? R(GAUSS_S) : R(-GAUSS_S);
+                X[(d + 2) % 3] = gb ? R(GAUSS_S) : R(-GAUSS_S);
+                R W[5];
+#pragma unroll
+                for (int v = 0; v < 5; ++v) W[v] = qcv[v] + poly9(cf[v], X);
+                const R p = (gamma - R(1)) * (W[4] - R(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / W[0]);
+                if (W[0] < R(0) || p < R(0)) bad = true;
+            }
+        }
+        bad = __any_sync(FULL, bad);
+        if (lane == owner) {
+            if (bad) {
+                for (int v = 0; v < 5; ++v)
+                    for (int n = 1; n < 10; ++n) coef[coef_slot(v, n) * g.cstride + t] = R(0);
+                atomicAdd(&ctl->flagged, 1);
+            }
+            flag[t] = bad ? 1 : 0;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -16,7 +16,15 @@ __global__ void __launch_bounds__(128) k_recon(const double *__restrict__ Q, R *
                                                unsigned char *__restrict__ flag, Geo g, Scheme S, Ctl *ctl)
 {
     if (!ctl->active) return;
-    recon_item<R>(Q, coef, flag, g, S, ctl, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    recon_item<R, true>(Q, coef, flag, g, S, ctl, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) k_positivity(const double *__restrict__ Q, R *__restrict__ coef,
+                                                    unsigned char *__restrict__ flag, Geo g, Scheme S, Ctl *ctl)
+{
+    if (!ctl->active) return;
+    positivity_item<R>(Q, coef, flag, g, S, ctl, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 template <typename R, int D>
@@ -179,6 +187,7 @@ void launch_recon(const double *Q, R *coef, unsigned char *flag, const Geo &g, c
                   cudaStream_t s)
 {
     k_recon<R><<<blocks_for(g.cstride, 128), 128, 0, s>>>(Q, coef, flag, g, S, ctl);
+    k_positivity<R><<<blocks_for(g.cstride, 128), 128, 0, s>>>(Q, coef, flag, g, S, ctl);
 }
 
 template <typename R>

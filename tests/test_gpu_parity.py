@@ -378,3 +378,35 @@ def test_device_buffers_through_the_abi():
     hgks.hgks_get_state(s.h, out)
     assert np.array_equal(out.cpu().numpy(), q0)
     s.close()
+
+
+def test_octant64_mixed_against_fp64():
+    """The octant Riemann workload in mixed precision at 64^3 (reflective):
+    L at sampled cells against the FP64 oracle on the common scale, and ten
+    steps against the FP64 path (parity-tested against the oracle above),
+    L1 and max of the density difference."""
+    n = (64, 64, 64)
+    lo, hi = (0, 0, 0), (1, 1, 1)
+    q0 = W.octant_riemann(n, seed=0)
+    cfg = oracle.make_cfg(n, lo, hi, bc=(1,) * 6)
+    dt = oracle.cfl_dt(cfg, q0, 0.35)
+    cells = [i + 64 * (j + 64 * k) for (i, j, k) in [(31, 31, 31), (32, 32, 32), (0, 0, 0), (63, 63, 63),
+                                                      (31, 5, 50), (0, 32, 63), (32, 31, 0), (10, 40, 31)]]
+    Lo, _ = oracle.operator(cfg, q0, dt, cells=cells)
+    res = {}
+    for prec in (hgks.HGKS_FP64, hgks.HGKS_MIXED):
+        s = _solver(n, lo, hi, bc=(1,) * 6, precision=prec)
+        s.set_state(q0)
+        L, _ = s.flux(dt)
+        if prec == hgks.HGKS_MIXED:
+            Ls = L.reshape(5, -1)[:, cells]
+            assert np.abs(Ls - Lo).max() <= 1e-4 * np.abs(Lo).max(), np.abs(Ls - Lo).max() / np.abs(Lo).max()
+        s.step(10, dt_fixed=dt)
+        res[prec], _ = s.get_state()
+        s.close()
+    d = np.abs(res[hgks.HGKS_MIXED][0] - res[hgks.HGKS_FP64][0])
+    l1 = float(d.mean())
+    linf = float(d.max())
+    print(f"octant 64^3, 10 steps: mixed - FP64 density L1 {l1:.3e}, Linf {linf:.3e}")
+    assert l1 <= 1e-5 * float(np.abs(res[hgks.HGKS_FP64][0]).mean())
+    assert linf <= 1e-3 * float(np.abs(res[hgks.HGKS_FP64][0]).max())
