@@ -53,6 +53,10 @@ enum { HGKS_FP64 = 0,   /* every operation in FP64                              
 
 enum { HGKS_BC_PERIODIC = 0, HGKS_BC_REFLECTIVE = 1, HGKS_BC_OUTFLOW = 2 };
 
+/* Largest number of cells along one axis (index arithmetic on the device is
+ * 32-bit); larger grids give HGKS_E_INVALID. */
+#define HGKS_MAX_CELLS_PER_AXIS 1024
+
 enum {
     HGKS_OK = 0,
     HGKS_E_INVALID = -1,     /* bad argument                                     */

@@ -167,7 +167,7 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
     *out = nullptr;
     for (int d = 0; d < 3; ++d) {
         // two ghost layers mirror or wrap at most two interior cells
-        if (grid->n[d] < 2 || !(grid->hi[d] > grid->lo[d]) ||
+        if (grid->n[d] < 2 || grid->n[d] > HGKS_MAX_CELLS_PER_AXIS || !(grid->hi[d] > grid->lo[d]) ||
             (grid->n[d] < hk::GHOST && (bc[2 * d] == HGKS_BC_REFLECTIVE || bc[2 * d + 1] == HGKS_BC_REFLECTIVE)))
             return fail(nullptr, HGKS_E_INVALID, "each axis needs at least 2 cells and hi > lo%s");
     }
@@ -537,7 +537,7 @@ extern "C" int hgks_step(hgks_t *h, int nsteps, double cfl, double dt_fixed, dou
                     hk::launch_cfl_mapped(h->Qn, h->geo, g, h->S.gamma, h->ctl, s);
                     ++nl;
                 } else {
-                    hk::launch_cfl(h->Qn, g, h->S.gamma, h->ctl, s);
+                    hk::launch_cfl(h->Qn, g, h->S.gamma, h->ctl, s, h->precision == HGKS_MIXED);
                 }
                 ++nl;
             }

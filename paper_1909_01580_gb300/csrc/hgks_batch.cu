@@ -36,6 +36,7 @@ struct BInst {
     double *F[3];
     Ctl *ctl;
     double cfl, t_end;
+    int mixed;  // FP32 CFL candidates, as on a single handle of the mixed path
 };
 
 // a tile: items [first, last) of one instance in one phase
@@ -81,7 +82,9 @@ __global__ void __launch_bounds__(256) kb_cfl(const BInst *__restrict__ I, const
         double v = INFINITY;
         for (long long b = T.first; b < T.last; b += blockDim.x) {
             const long long t = b + threadIdx.x;
-            if (t < T.last) v = fmin(v, hk::cfl_value(in.Qn, in.g, in.S.gamma, t));
+            if (t < T.last)
+                v = fmin(v, in.mixed ? hk::cfl_value_mixed(in.Qn, in.g, in.S.gamma, t)
+                                     : hk::cfl_value(in.Qn, in.g, in.S.gamma, t));
         }
         hk::block_min_to(v, &in.ctl->minbits);
     }
@@ -220,7 +223,8 @@ static int validate_grid(const hgks_grid_t *grid, double gamma, double mu, doubl
 {
     if (!grid || !bc) return HGKS_E_INVALID;
     for (int d = 0; d < 3; ++d) {
-        if (grid->n[d] < 2 || !(grid->hi[d] > grid->lo[d])) return HGKS_E_INVALID;
+        if (grid->n[d] < 2 || grid->n[d] > HGKS_MAX_CELLS_PER_AXIS || !(grid->hi[d] > grid->lo[d]))
+            return HGKS_E_INVALID;
         if (grid->n[d] < hk::GHOST && (bc[2 * d] == HGKS_BC_REFLECTIVE || bc[2 * d + 1] == HGKS_BC_REFLECTIVE))
             return HGKS_E_INVALID;
     }
@@ -537,6 +541,7 @@ extern "C" int hgks_batch_add(hgks_batch_t *b, const hgks_grid_t *grid, double g
     if (!arena_take(b, tot, &off)) return bfail(b, HGKS_E_NOMEM, "not enough free arena memory for this instance");
     BInst &in = b->inst[sl];
     in.g = g;
+    in.mixed = b->precision == HGKS_MIXED;
     Scheme &S = in.S;
     S.gamma = gamma;
     S.K = (5.0 - 3.0 * gamma) / (gamma - 1.0);

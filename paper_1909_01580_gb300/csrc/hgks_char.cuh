@@ -135,9 +135,7 @@ __device__ __forceinline__ void char_face_cells(const Geo &g, long long face, in
                                                 int rc[3])
 {
     const int ex = g.nx + (D == 0), ey = g.ny + (D == 1);
-    rc[0] = (int)(face % ex);
-    rc[1] = (int)((face / ex) % ey);
-    rc[2] = (int)(face / ((long long)ex * ey));
+    split3(face, ex, ey, rc[0], rc[1], rc[2]);
 #pragma unroll
     for (int e = 0; e < 3; ++e) lc[e] = rc[e] - (e == D);
 #pragma unroll

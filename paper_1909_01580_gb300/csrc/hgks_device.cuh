@@ -124,6 +124,17 @@ HK_HD long long pidx(const Geo &g, int i, int j, int k)
 {
     return ((long long)(k + GHOST) * g.py + (j + GHOST)) * g.px + (i + GHOST);
 }
+// linear index -> (i, j, k) of an a x b x * box in 32-bit arithmetic (every
+// box and face count of a handle fits: sizes are capped at creation)
+HK_HD void split3(long long t, int a, int b, int &i, int &j, int &k)
+{
+    const unsigned u = (unsigned)t, ua = (unsigned)a, ub = (unsigned)b;
+    const unsigned r = u / ua;
+    i = (int)(u - r * ua);
+    k = (int)(r / ub);
+    j = (int)(r - (unsigned)k * ub);
+}
+
 HK_HD long long cidx(const Geo &g, int i, int j, int k)
 {
     return ((long long)(k + 1) * g.cy + (j + 1)) * g.cx + (i + 1);

@@ -21,7 +21,8 @@ namespace hk {
 __device__ __forceinline__ void halo_item(double *__restrict__ Q, const Geo &g, long long t)
 {
     if (t >= g.pstride) return;
-    const int ip = (int)(t % g.px), jp = (int)((t / g.px) % g.py), kp = (int)(t / ((long long)g.px * g.py));
+    int ip, jp, kp;
+    split3(t, g.px, g.py, ip, jp, kp);
     const int idx[3] = {ip - GHOST, jp - GHOST, kp - GHOST};
     const int n[3] = {g.nx, g.ny, g.nz};
     int src[3];
@@ -182,7 +183,11 @@ __device__ __forceinline__ void recon_item(const double *__restrict__ Q, R *__re
                                            long long t)
 {
     if (t >= g.cstride) return;
-    const int i = (int)(t % g.cx) - 1, j = (int)((t / g.cx) % g.cy) - 1, k = (int)(t / ((long long)g.cx * g.cy)) - 1;
+    int i, j, k;
+    split3(t, g.cx, g.cy, i, j, k);
+    i -= 1;
+    j -= 1;
+    k -= 1;
     R rad[5], qcv[5];
 #pragma unroll 1
     for (int v = 0; v < 5; ++v) {
@@ -241,7 +246,11 @@ __device__ __forceinline__ void positivity_item(const double *__restrict__ Q, R 
         const int owner = __ffs(pending) - 1;
         pending &= pending - 1;
         const long long tc = __shfl_sync(FULL, t, owner);
-        const int i = (int)(tc % g.cx) - 1, j = (int)((tc / g.cx) % g.cy) - 1, k = (int)(tc / ((long long)g.cx * g.cy)) - 1;
+        int i, j, k;
+        split3(tc, g.cx, g.cy, i, j, k);
+        i -= 1;
+        j -= 1;
+        k -= 1;
         bool bad = false;
         if (lane < npoly) {
             R cf[5][9], qcv[5];
@@ -361,7 +370,8 @@ __device__ __forceinline__ void flux_item(const R *__restrict__ coef, double *__
     const bool valid = face < nface && t < tlimit;
     if (!valid) face = nface - 1;
     // (i, j, k) is the right cell; the left cell is one step back along D
-    const int i = (int)(face % ex), j = (int)((face / ex) % ey), k = (int)(face / ((long long)ex * ey));
+    int i, j, k;
+    split3(face, ex, ey, i, j, k);
     const int il = i - (D == 0), jl = j - (D == 1), kl = k - (D == 2);
     const R xa = (gp & 2) ? R(GAUSS_S) : R(-GAUSS_S);
     const R xb = (gp & 1) ? R(GAUSS_S) : R(-GAUSS_S);
@@ -437,7 +447,8 @@ __device__ __forceinline__ void update_item(double *__restrict__ Qn, double *__r
         ctl->steps_done += 1;
     }
     if (t >= g.ncell) return;
-    const int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / ((long long)g.nx * g.ny));
+    int i, j, k;
+    split3(t, g.nx, g.ny, i, j, k);
     double L[5], dL[5];
     cell_residual(Fx, Fy, Fz, g, i, j, k, L, dL);
     const long long pi = pidx(g, i, j, k);
@@ -455,8 +466,10 @@ __device__ __forceinline__ void update_item(double *__restrict__ Qn, double *__r
             W[v] = Wacc[v * g.ncell + t] + (dt * dt / 3.0) * dL[v];
             Qn[v * g.pstride + pi] = W[v];
         }
-        const double p = (gamma - 1.0) * (W[4] - 0.5 * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / W[0]);
-        if (!(W[0] > 0.0) || !(p > 0.0)) atomicOr(&ctl->status, 1);
+        // p > 0 with rho > 0 is 2 rho E > |rho U|^2 (no division)
+        const double m2 = W[1] * W[1] + W[2] * W[2] + W[3] * W[3];
+        if (!(W[0] > 0.0) || !(2.0 * W[4] * W[0] > m2)) atomicOr(&ctl->status, 1);
+        (void)gamma;
     }
 }
 
@@ -470,7 +483,8 @@ __device__ __forceinline__ void update_item(double *__restrict__ Qn, double *__r
 __device__ __forceinline__ double cfl_value(const double *__restrict__ Q, const Geo &g, double gamma, long long t)
 {
     if (t >= g.ncell) return INFINITY;
-    const int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / ((long long)g.nx * g.ny));
+    int i, j, k;
+    split3(t, g.nx, g.ny, i, j, k);
     const long long pi = pidx(g, i, j, k);
     double W[5];
 #pragma unroll
@@ -483,6 +497,28 @@ __device__ __forceinline__ double cfl_value(const double *__restrict__ Q, const 
     double v = g.h / (speed + c);
     if (!(v > 0.0)) v = 0.0;  // nonphysical: force dt = 0
     return v;
+}
+
+// the same candidate with the arithmetic in FP32 (the mixed path: FP32
+// candidates, FP64 minimum); a cell whose FP32 pressure is not clearly
+// positive is recomputed in FP64, so that round-off never reads as a
+// nonphysical state
+__device__ __forceinline__ double cfl_value_mixed(const double *__restrict__ Q, const Geo &g, double gamma,
+                                                  long long t)
+{
+    if (t >= g.ncell) return INFINITY;
+    int i, j, k;
+    split3(t, g.nx, g.ny, i, j, k);
+    const long long pi = pidx(g, i, j, k);
+    float W[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) W[q] = float(Q[q * g.pstride + pi]);
+    const float ir = 1.0f / W[0];
+    const float m2 = W[1] * W[1] + W[2] * W[2] + W[3] * W[3];
+    const float p = float(gamma - 1.0) * (W[4] - 0.5f * m2 * ir);
+    if (!(W[0] > 0.0f) || !(p > 1e-4f * W[4])) return cfl_value(Q, g, gamma, t);
+    const float s = sqrtf(m2) * ir + sqrtf(float(gamma) * p * ir);
+    return double(float(g.h) / s);
 }
 
 // all threads of the block call it (blockDim a multiple of 32, <= 1024)

@@ -51,7 +51,8 @@ __global__ void k_residual(const double *__restrict__ Fx, const double *__restri
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.ncell) return;
-    const int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / ((long long)g.nx * g.ny));
+    int i, j, k;
+    split3(t, g.nx, g.ny, i, j, k);
     double l[5], dl[5];
     cell_residual(Fx, Fy, Fz, g, i, j, k, l, dl);
 #pragma unroll
@@ -61,9 +62,11 @@ __global__ void k_residual(const double *__restrict__ Fx, const double *__restri
     }
 }
 
+template <bool MIXED>
 __global__ void __launch_bounds__(256) k_cfl(const double *__restrict__ Q, Geo g, double gamma, Ctl *ctl)
 {
-    block_min_to(cfl_value(Q, g, gamma, (long long)blockIdx.x * blockDim.x + threadIdx.x), &ctl->minbits);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    block_min_to(MIXED ? cfl_value_mixed(Q, g, gamma, t) : cfl_value(Q, g, gamma, t), &ctl->minbits);
 }
 
 // one thread: choose dt for this step and arm the stage kernels
@@ -97,7 +100,8 @@ __global__ void k_scatter(const double *__restrict__ src, double *__restrict__ Q
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.ncell) return;
-    const int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / ((long long)g.nx * g.ny));
+    int i, j, k;
+    split3(t, g.nx, g.ny, i, j, k);
     const long long pi = pidx(g, i, j, k);
 #pragma unroll
     for (int v = 0; v < 5; ++v) Q[v * g.pstride + pi] = src[v * g.ncell + t];
@@ -106,7 +110,8 @@ __global__ void k_gather(const double *__restrict__ Q, double *__restrict__ dst,
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.ncell) return;
-    const int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / ((long long)g.nx * g.ny));
+    int i, j, k;
+    split3(t, g.nx, g.ny, i, j, k);
     const long long pi = pidx(g, i, j, k);
 #pragma unroll
     for (int v = 0; v < 5; ++v) dst[v * g.ncell + t] = Q[v * g.pstride + pi];
@@ -119,7 +124,8 @@ __global__ void k_export_coef(const R *__restrict__ coef, const unsigned char *_
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.ncell) return;
-    const int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / ((long long)g.nx * g.ny));
+    int i, j, k;
+    split3(t, g.nx, g.ny, i, j, k);
     const long long ci = cidx(g, i, j, k);
     for (int v = 0; v < 5; ++v)
         for (int n = 0; n < 9; ++n) out[t * 45 + v * 9 + n] = double(coef[coef_slot(v, 1 + n) * g.cstride + ci]);
@@ -213,9 +219,10 @@ void launch_residual(const double *Fx, const double *Fy, const double *Fz, const
     k_residual<<<blocks_for(g.ncell, 256), 256, 0, s>>>(Fx, Fy, Fz, g, L, dL);
 }
 
-void launch_cfl(const double *Q, const Geo &g, double gamma, Ctl *ctl, cudaStream_t s)
+void launch_cfl(const double *Q, const Geo &g, double gamma, Ctl *ctl, cudaStream_t s, bool mixed)
 {
-    k_cfl<<<blocks_for(g.ncell, 256), 256, 0, s>>>(Q, g, gamma, ctl);
+    if (mixed) k_cfl<true><<<blocks_for(g.ncell, 256), 256, 0, s>>>(Q, g, gamma, ctl);
+    else k_cfl<false><<<blocks_for(g.ncell, 256), 256, 0, s>>>(Q, g, gamma, ctl);
 }
 
 void launch_dt(Ctl *ctl, double cfl, double dt_fixed, double t_end, cudaStream_t s)

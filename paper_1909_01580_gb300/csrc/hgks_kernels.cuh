@@ -14,7 +14,8 @@ void launch_update(int stage, double *Qn, double *Qs, double *Wacc, const double
                    const double *Fz, const Geo &g, double gamma, Ctl *ctl, cudaStream_t s);
 void launch_residual(const double *Fx, const double *Fy, const double *Fz, const Geo &g, double *L, double *dL,
                      cudaStream_t s);
-void launch_cfl(const double *Q, const Geo &g, double gamma, Ctl *ctl, cudaStream_t s);
+// mixed: FP32 candidates (FP64 minimum) for the mixed path
+void launch_cfl(const double *Q, const Geo &g, double gamma, Ctl *ctl, cudaStream_t s, bool mixed = false);
 void launch_dt(Ctl *ctl, double cfl, double dt_fixed, double t_end, cudaStream_t s);
 void launch_init_ctl(Ctl *ctl, double t, cudaStream_t s);
 void launch_set_ctl(Ctl *ctl, double t, double dt, int active, cudaStream_t s);

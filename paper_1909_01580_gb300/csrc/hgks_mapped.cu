@@ -15,8 +15,11 @@ __global__ void __launch_bounds__(128) k_geom(double *__restrict__ geo, Geo g, M
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.pstride) return;
-    const int i = (int)(t % g.px) - GHOST, j = (int)((t / g.px) % g.py) - GHOST,
-              k = (int)(t / ((long long)g.px * g.py)) - GHOST;
+    int i, j, k;
+    split3(t, g.px, g.py, i, j, k);
+    i -= GHOST;
+    j -= GHOST;
+    k -= GHOST;
     const double ts = ctl ? stage_time(ctl, half) : t_fixed;
     const double Sf = map_factor(m, ts);
     if (ctl && t == 0) {
@@ -35,7 +38,8 @@ __global__ void k_vol_from_geo(const double *__restrict__ geo, double *__restric
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.ncell) return;
-    const int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / ((long long)g.nx * g.ny));
+    int i, j, k;
+    split3(t, g.nx, g.ny, i, j, k);
     vol[t] = geo[pidx(g, i, j, k)];
 }
 
@@ -88,7 +92,8 @@ __global__ void k_residual_mapped(const double *__restrict__ Fx, const double *_
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.ncell) return;
-    const int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / ((long long)g.nx * g.ny));
+    int i, j, k;
+    split3(t, g.nx, g.ny, i, j, k);
     double Rr[5], dR[5], V;
     cell_residual_mapped(Fx, Fy, Fz, g, i, j, k, Rr, dR, V);
     const double vol = geo[pidx(g, i, j, k)];
@@ -106,7 +111,8 @@ __global__ void __launch_bounds__(256) k_cfl_mapped(const double *__restrict__ Q
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double v = INFINITY;
     if (t < g.ncell) {
-        const int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / ((long long)g.nx * g.ny));
+        int i, j, k;
+        split3(t, g.nx, g.ny, i, j, k);
         const long long pi = pidx(g, i, j, k);
         double W[5];
 #pragma unroll

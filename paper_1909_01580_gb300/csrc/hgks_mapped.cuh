@@ -601,7 +601,11 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
                                                   R *sh, long long t)
 {
     if (t >= g.cstride) return;
-    const int i = (int)(t % g.cx) - 1, j = (int)((t / g.cx) % g.cy) - 1, k = (int)(t / ((long long)g.cx * g.cy)) - 1;
+    int i, j, k;
+    split3(t, g.cx, g.cy, i, j, k);
+    i -= 1;
+    j -= 1;
+    k -= 1;
     CellFrame<R> F;
     make_frame(geo, g, i, j, k, F);
     const double ih = 1.0 / F.h;
@@ -828,7 +832,11 @@ __device__ __forceinline__ void positivity_mapped_item(const double *__restrict_
                                                        Ctl *ctl, long long t)
 {
     if (t >= g.cstride || flag[t] != 2) return;
-    const int i = (int)(t % g.cx) - 1, j = (int)((t / g.cx) % g.cy) - 1, k = (int)(t / ((long long)g.cx * g.cy)) - 1;
+    int i, j, k;
+    split3(t, g.cx, g.cy, i, j, k);
+    i -= 1;
+    j -= 1;
+    k -= 1;
     CellFrame<R> F;
     make_frame(geo, g, i, j, k, F);
     const bool bad = positivity_violated_mapped<R>(Q, geo, g, m, S, i, j, k, F, R(Sch.gamma));
@@ -894,7 +902,8 @@ __device__ __forceinline__ void flux_mapped_item(const R *__restrict__ coef, dou
     const int gp = (int)(t & 3);
     const bool valid = face < nface;
     if (!valid) face = nface - 1;
-    const int i = (int)(face % ex), j = (int)((face / ex) % ey), k = (int)(face / ((long long)ex * ey));
+    int i, j, k;
+    split3(face, ex, ey, i, j, k);
     const int il = i - (D == 0), jl = j - (D == 1), kl = k - (D == 2);
     constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
     const R ea = (gp & 2) ? R(GAUSS_S) : R(-GAUSS_S), eb = (gp & 1) ? R(GAUSS_S) : R(-GAUSS_S);
@@ -1056,7 +1065,8 @@ __device__ __forceinline__ void update_mapped_item(double *__restrict__ Qn, doub
         ctl->steps_done += 1;
     }
     if (t >= g.ncell) return;
-    const int i = (int)(t % g.nx), j = (int)((t / g.nx) % g.ny), k = (int)(t / ((long long)g.nx * g.ny));
+    int i, j, k;
+    split3(t, g.nx, g.ny, i, j, k);
     double Rr[5], dR[5], V;
     cell_residual_mapped(Fx, Fy, Fz, g, i, j, k, Rr, dR, V);
     const long long pi = pidx(g, i, j, k);

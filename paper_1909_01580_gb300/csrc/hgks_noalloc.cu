@@ -71,7 +71,7 @@ extern "C" int hgks_flux_noalloc(const hgks_grid_t *grid, double gamma, double m
         return HGKS_E_INVALID;
     }
     for (int d = 0; d < 3; ++d) {
-        if (grid->n[d] < 2 || !(grid->hi[d] > grid->lo[d]) ||
+        if (grid->n[d] < 2 || grid->n[d] > HGKS_MAX_CELLS_PER_AXIS || !(grid->hi[d] > grid->lo[d]) ||
             (grid->n[d] < hk::GHOST && (bc[2 * d] == HGKS_BC_REFLECTIVE || bc[2 * d + 1] == HGKS_BC_REFLECTIVE))) {
             hgks_internal_set_error("hgks_flux_noalloc: each axis needs at least 2 cells and hi > lo");
             return HGKS_E_INVALID;
