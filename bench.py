@@ -42,8 +42,8 @@ UNIT = "cell-stage updates/s"
 # capture, scaled by the faces of a 128^3 launch (traffic grows with the
 # cells: the coefficient array is read once).
 FLUX_FP64_FLOP_PER_GP = 3042.0
-FLUX_FP32_FLOP_PER_GP = 2842.0
-FLUX_TRAFFIC_BYTES_PER_FACE = {"fp64": 14.308e6 / 33792, "mixed": 7.218e6 / 33792}
+FLUX_FP32_FLOP_PER_GP = 2845.0
+FLUX_TRAFFIC_BYTES_PER_FACE = {"fp64": 14.306e6 / 33792, "mixed": 7.215e6 / 33792}
 # GB300 ALU peaks derived from unit counts and clocks: 152 SMs x 2070 MHz x
 # (FP64: 2 DFMA/clk/SM = 4 flop; FP32: 128 FMA/clk/SM = 256 flop).
 SM_COUNT = 152
@@ -411,6 +411,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the small serving run of the default line")
     ap.add_argument("--no-moving", action="store_true", help="skip the 96^3 moving-mesh run of the default line")
+    ap.add_argument("--moving-n", type=int, default=96, help="cells per axis of the moving-mesh run")
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the octant-Riemann and isotropic-turbulence runs of the default line")
     ap.add_argument("--serving", action="store_true",
@@ -471,7 +472,7 @@ def main():
             line["e2e"] = main_r["e2e"]
             line["mixed"]["e2e"] = res["mixed"].get("e2e")
         if not args.no_moving and world == 1:
-            line["moving_mesh"] = moving_run(steps=max(1, min(args.steps, 5)), warmup=2)
+            line["moving_mesh"] = moving_run(steps=max(1, min(args.steps, 5)), warmup=2, n=args.moving_n)
         if not args.no_workloads and world == 1:
             line["octant_riemann"] = octant_run(steps=max(1, min(args.steps, 5)), warmup=2)
             line["isotropic_turbulence"] = turbulence_run(steps=max(1, min(args.steps, 5)), warmup=2)
