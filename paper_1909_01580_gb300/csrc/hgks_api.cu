@@ -37,6 +37,9 @@ struct hgks {
     double *geo;                 // [NGEO][pstride] cell geometry at the stage time
     double *vol, *vnext;         // [ncell] volumes of the discrete conservation law
     double *sintab;              // sine factors of the map at the vertex indices
+    // mixed path on the uniform mesh: the split state Q_hi + Q_lo in FP32
+    // ([2][5][pstride]) that the reconstruction takes its differences from
+    float *Qsplit;
     // reconstruction in characteristic variables (option "characteristic")
     int charvar;
     void *coefc[3];              // per axis [2][50][nface_d] in the working precision
@@ -158,6 +161,7 @@ static void free_all(hgks_t *h)
         cudaFree(h->coefc[d]);
         cudaFree(h->flagc[d]);
     }
+    cudaFree(h->Qsplit);
 }
 
 extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, double Pr, const int bc[6], void *stream,
@@ -257,6 +261,11 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
         ok = cudaMalloc(ptrs[i], sizes[i]) == cudaSuccess;
         h->bytes += sizes[i];
     }
+    if (ok && !mapped && grid->precision == HGKS_MIXED) {
+        const size_t b = 2 * 5 * g.pstride * sizeof(float);
+        ok = cudaMalloc((void **)&h->Qsplit, b) == cudaSuccess;
+        h->bytes += b;
+    }
     for (int d = 0; d < 3 && ok; ++d) {
         size_t b = nfv * nface(g, d) * sizeof(double);
         ok = cudaMalloc((void **)&h->F[d], b) == cudaSuccess;
@@ -273,12 +282,17 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
                 const double xi = grid->lo[d] + (grid->hi[d] - grid->lo[d]) * (double)iv / (double)grid->n[d];
                 tab[o] = sin(2.0 * M_PI * (xi - grid->lo[d]) / (grid->hi[d] - grid->lo[d]));
             }
-        ok = cudaMalloc((void **)&h->sintab, tab.size() * sizeof(double)) == cudaSuccess &&
-             cudaMemcpy(h->sintab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+        // the same factors in FP32 after the FP64 ones, in one allocation
+        std::vector<float> tabf(tab.begin(), tab.end());
+        const size_t tbytes = tab.size() * sizeof(double) + tabf.size() * sizeof(float);
+        ok = cudaMalloc((void **)&h->sintab, tbytes) == cudaSuccess &&
+             cudaMemcpy(h->sintab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(h->sintab + tab.size(), tabf.data(), tabf.size() * sizeof(float), cudaMemcpyHostToDevice) ==
+                 cudaSuccess;
         ok = ok && cudaMalloc((void **)&h->geo, hk::NGEO * g.pstride * sizeof(double)) == cudaSuccess;
         ok = ok && cudaMalloc((void **)&h->vol, g.ncell * sizeof(double)) == cudaSuccess;
         ok = ok && cudaMalloc((void **)&h->vnext, g.ncell * sizeof(double)) == cudaSuccess;
-        h->bytes += tab.size() * sizeof(double) + (hk::NGEO * g.pstride + 2 * g.ncell) * sizeof(double);
+        h->bytes += tbytes + (hk::NGEO * g.pstride + 2 * g.ncell) * sizeof(double);
         for (int d = 0; d < 3; ++d) {
             h->map.lo[d] = grid->lo[d];
             h->map.hi[d] = grid->hi[d];
@@ -290,6 +304,14 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
         h->map.sx = h->sintab;
         h->map.sy = h->sintab + nv[0];
         h->map.sz = h->sintab + nv[0] + nv[1];
+        const float *tf = (const float *)(h->sintab + tab.size());
+        h->map.sxf = tf;
+        h->map.syf = tf + nv[0];
+        h->map.szf = tf + nv[0] + nv[1];
+        for (int d = 0; d < 3; ++d) {
+            h->map.lof[d] = float(grid->lo[d]);
+            h->map.hf[d] = float((grid->hi[d] - grid->lo[d]) / grid->n[d]);
+        }
     }
     ok = ok && cudaMalloc((void **)&h->ctl, sizeof(Ctl)) == cudaSuccess;
     ok = ok && cudaMallocHost((void **)&h->ctl_host, sizeof(Ctl)) == cudaSuccess;
@@ -499,8 +521,8 @@ static int stage_fluxes(hgks_t *h, double *Q, int half = 0, bool geom_ready = fa
     if (h->precision == HGKS_MIXED) {
         float *c = (float *)h->coef;
         {
-            PhaseTimer t(h, HGKS_PHASE_RECON, 2);
-            hk::launch_recon<float>(Q, c, h->flag, g, h->S, h->ctl, s);
+            PhaseTimer t(h, HGKS_PHASE_RECON, 3);
+            hk::launch_recon<float>(Q, c, h->flag, g, h->S, h->ctl, s, h->Qsplit);
         }
         PhaseTimer t(h, HGKS_PHASE_FLUX, 3);
         for (int d = 0; d < 3; ++d) hk::launch_flux<float>(d, c, h->F[d], g, h->S, h->ctl, s);
@@ -513,8 +535,9 @@ static int stage_fluxes(hgks_t *h, double *Q, int half = 0, bool geom_ready = fa
         PhaseTimer t(h, HGKS_PHASE_FLUX, 3);
         for (int d = 0; d < 3; ++d) hk::launch_flux<double>(d, c, h->F[d], g, h->S, h->ctl, s);
     }
-    // halo, reconstruction and its positivity pass, three face sweeps
-    return check_launch(h, 6);
+    // halo, (split state,) reconstruction and its positivity pass, three face
+    // sweeps
+    return check_launch(h, 6 + (h->Qsplit ? 1 : 0));
 }
 
 extern "C" int hgks_step(hgks_t *h, int nsteps, double cfl, double dt_fixed, double t_end, double *t_out,
@@ -642,7 +665,7 @@ extern "C" int hgks_reconstruct(hgks_t *h, double *coef, int *flag)
     if (h->mesh != 0) hk::launch_geom(h->geo, g, h->map, h->ctl, 0, 0.0, s);
     if (h->precision == HGKS_MIXED) {
         if (h->mesh != 0) hk::launch_recon_mapped<float>(h->Qn, h->geo, (float *)h->coef, h->flag, g, h->map, h->S, h->ctl, 0, s);
-        else hk::launch_recon<float>(h->Qn, (float *)h->coef, h->flag, g, h->S, h->ctl, s);
+        else hk::launch_recon<float>(h->Qn, (float *)h->coef, h->flag, g, h->S, h->ctl, s, h->Qsplit);
         hk::launch_export_coef<float>((float *)h->coef, h->flag, g, dc, df, s);
     } else {
         if (h->mesh != 0) hk::launch_recon_mapped<double>(h->Qn, h->geo, (double *)h->coef, h->flag, g, h->map, h->S, h->ctl, 0, s);
@@ -652,7 +675,7 @@ extern "C" int hgks_reconstruct(hgks_t *h, double *coef, int *flag)
     hk::launch_set_ctl(h->ctl, h->ctl_host->t, 0.0, 0, s);
     // reconstruction, export and control reset; on a mapped mesh also the
     // geometry and the positivity pass
-    rc = check_launch(h, 4 + (h->mesh != 0 ? 1 : 0));
+    rc = check_launch(h, 4 + (h->mesh != 0 ? 1 : 0) + (h->Qsplit ? 1 : 0));
     if (!rc) {
         cudaMemcpyAsync(coef, dc, 45 * g.ncell * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (flag) cudaMemcpyAsync(flag, df, g.ncell * sizeof(int), cudaMemcpyDeviceToHost, s);

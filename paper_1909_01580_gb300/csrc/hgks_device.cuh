@@ -156,6 +156,7 @@ struct Ctl {
     int flagged;                 // cells that took the positivity fallback (last stage)
     double mapS, mapC;           // mapped mesh: sin(omega t), cos(omega t) at the stage time
                                  // (S = 1, C = 0 on a static mesh), set by the geometry kernel
+    float mapAS, mapAUC;         // amp S and amp omega C in FP32 (mixed path)
 };
 
 // ---------------------------------------------------------------------------

@@ -79,6 +79,59 @@ __device__ __forceinline__ void load_stencil(const double *__restrict__ Qv, cons
     }
 }
 
+// The mixed path's split state: Q = Q_hi + Q_lo with Q_hi = fl32(Q) and
+// Q_lo = fl32(Q - Q_hi) (about 48 significant bits together).  A difference
+// of neighbours formed as (hi_nb - hi_c) + (lo_nb - lo_c) in FP32 is the FP64
+// difference to about one FP32 rounding: the hi part is exact for values
+// within a factor 2 of each other (and otherwise rounds at the size of the
+// result), the lo part is 2^-24 smaller.  The reconstruction then needs no
+// FP64 arithmetic; the split is formed once per stage by k_split.
+__device__ __forceinline__ void split_item(const double *__restrict__ Q, float *__restrict__ hi,
+                                           float *__restrict__ lo, long long n, long long t)
+{
+    if (t >= n) return;
+    const double q = Q[t];
+    const float h = float(q);
+    hi[t] = h;
+    lo[t] = float(q - double(h));
+}
+
+// the stencil differences of one variable from the split state
+__device__ __forceinline__ void load_stencil_split(const float *__restrict__ hv, const float *__restrict__ lv,
+                                                   const Geo &g, int i, int j, int k, Stencil<float> &st)
+{
+    const long long sd[3] = {1, g.px, (long long)g.px * g.py};
+    const long long c = pidx(g, i, j, k);
+    const float hc = hv[c], lc = lv[c];
+    auto diff = [&](long long at) { return (hv[at] - hc) + (lv[at] - lc); };
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        st.f[d][0] = diff(c - sd[d]);
+        st.f[d][1] = diff(c + sd[d]);
+    }
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const long long a = sd[p], b = sd[(p + 1) % 3];
+#pragma unroll
+        for (int sa = 0; sa < 2; ++sa)
+#pragma unroll
+            for (int sb = 0; sb < 2; ++sb) st.e[p][sa][sb] = diff(c + (sa ? a : -a) + (sb ? b : -b));
+    }
+}
+
+__device__ __forceinline__ void load_stencil_split_far(const float *__restrict__ hv, const float *__restrict__ lv,
+                                                       const Geo &g, int i, int j, int k, Stencil<float> &st)
+{
+    const long long sd[3] = {1, g.px, (long long)g.px * g.py};
+    const long long c = pidx(g, i, j, k);
+    const float hc = hv[c], lc = lv[c];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        st.f2[d][0] = (hv[c - 2 * sd[d]] - hc) + (lv[c - 2 * sd[d]] - lc);
+        st.f2[d][1] = (hv[c + 2 * sd[d]] - hc) + (lv[c + 2 * sd[d]] - lc);
+    }
+}
+
 // the six axis cells two steps away, for S' (formed in FP64 like the rest)
 template <typename R>
 __device__ __forceinline__ void load_stencil_far(const double *__restrict__ Qv, const Geo &g, int i, int j, int k,
@@ -177,10 +230,12 @@ __device__ __noinline__ bool positivity_violated_sp(const double *__restrict__ Q
 // SPLIT: leave the literal positivity check to positivity_item (a kernel of
 // its own, whose register demand then does not weigh on this one) and mark
 // the cells whose bound is inconclusive with flag 2
-template <typename R, bool SPLIT = false>
+// QS (mixed path): the differences come from the split state Qsplit,
+// [hi: 5][pstride] then [lo: 5][pstride]
+template <typename R, bool SPLIT = false, bool QS = false>
 __device__ __forceinline__ void recon_item(const double *__restrict__ Q, R *__restrict__ coef,
                                            unsigned char *__restrict__ flag, const Geo &g, const Scheme &S, Ctl *ctl,
-                                           long long t)
+                                           long long t, const float *__restrict__ Qsplit = nullptr)
 {
     if (t >= g.cstride) return;
     int i, j, k;
@@ -192,17 +247,22 @@ __device__ __forceinline__ void recon_item(const double *__restrict__ Q, R *__re
 #pragma unroll 1
     for (int v = 0; v < 5; ++v) {
         const double *Qv = Q + v * g.pstride;
-        const double qc = Qv[pidx(g, i, j, k)];
-        qcv[v] = R(qc);
         Stencil<R> st;
-        load_stencil(Qv, g, i, j, k, qc, st);
-        R out[9];
-        if (S.sprime) {
-            load_stencil_far(Qv, g, i, j, k, qc, st);
-            weno_ao_sp(st, S, out, rad[v]);
+        double qc;
+        if constexpr (sizeof(R) == 4 && QS) {
+            const float *hv = Qsplit + v * g.pstride, *lv = Qsplit + (5 + v) * g.pstride;
+            qc = double(hv[pidx(g, i, j, k)]);  // fl32(Q_c), the value stored below
+            load_stencil_split(hv, lv, g, i, j, k, st);
+            if (S.sprime) load_stencil_split_far(hv, lv, g, i, j, k, st);
         } else {
-            weno_ao(st, S, out, rad[v]);
+            qc = Qv[pidx(g, i, j, k)];
+            load_stencil(Qv, g, i, j, k, qc, st);
+            if (S.sprime) load_stencil_far(Qv, g, i, j, k, qc, st);
         }
+        qcv[v] = R(qc);
+        R out[9];
+        if (S.sprime) weno_ao_sp(st, S, out, rad[v]);
+        else weno_ao(st, S, out, rad[v]);
         coef[coef_slot(v, 0) * g.cstride + t] = R(qc);
 #pragma unroll
         for (int n = 0; n < 9; ++n) coef[coef_slot(v, 1 + n) * g.cstride + t] = out[n];

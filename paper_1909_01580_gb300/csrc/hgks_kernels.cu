@@ -11,12 +11,18 @@ __global__ void k_halo(double *__restrict__ Q, Geo g)
     halo_item(Q, g, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-template <typename R>
+template <typename R, bool QS>
 __global__ void __launch_bounds__(128) k_recon(const double *__restrict__ Q, R *__restrict__ coef,
-                                               unsigned char *__restrict__ flag, Geo g, Scheme S, Ctl *ctl)
+                                               unsigned char *__restrict__ flag, Geo g, Scheme S, Ctl *ctl,
+                                               const float *__restrict__ Qsplit)
 {
     if (!ctl->active) return;
-    recon_item<R, true>(Q, coef, flag, g, S, ctl, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    recon_item<R, true, QS>(Q, coef, flag, g, S, ctl, (long long)blockIdx.x * blockDim.x + threadIdx.x, Qsplit);
+}
+
+__global__ void k_split(const double *__restrict__ Q, float *__restrict__ hi, float *__restrict__ lo, long long n)
+{
+    split_item(Q, hi, lo, n, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 template <typename R>
@@ -190,9 +196,14 @@ void launch_halo(double *Q, const Geo &g, cudaStream_t s)
 
 template <typename R>
 void launch_recon(const double *Q, R *coef, unsigned char *flag, const Geo &g, const Scheme &S, Ctl *ctl,
-                  cudaStream_t s)
+                  cudaStream_t s, float *split)
 {
-    k_recon<R><<<blocks_for(g.cstride, 128), 128, 0, s>>>(Q, coef, flag, g, S, ctl);
+    if (split) {
+        const long long n = 5 * g.pstride;
+        k_split<<<blocks_for(n, 256), 256, 0, s>>>(Q, split, split + n, n);
+    }
+    if (split) k_recon<R, true><<<blocks_for(g.cstride, 128), 128, 0, s>>>(Q, coef, flag, g, S, ctl, split);
+    else k_recon<R, false><<<blocks_for(g.cstride, 128), 128, 0, s>>>(Q, coef, flag, g, S, ctl, nullptr);
     k_positivity<R><<<blocks_for(g.cstride, 128), 128, 0, s>>>(Q, coef, flag, g, S, ctl);
 }
 
@@ -262,9 +273,9 @@ void launch_point_flux(int n, const double *in, const double *ug, double dt, con
 }
 
 template void launch_recon<double>(const double *, double *, unsigned char *, const Geo &, const Scheme &, Ctl *,
-                                   cudaStream_t);
+                                   cudaStream_t, float *);
 template void launch_recon<float>(const double *, float *, unsigned char *, const Geo &, const Scheme &, Ctl *,
-                                  cudaStream_t);
+                                  cudaStream_t, float *);
 template void launch_flux<double>(int, const double *, double *, const Geo &, const Scheme &, Ctl *, cudaStream_t);
 template void launch_flux<float>(int, const float *, double *, const Geo &, const Scheme &, Ctl *, cudaStream_t);
 template void launch_export_coef<double>(const double *, const unsigned char *, const Geo &, double *, int *,

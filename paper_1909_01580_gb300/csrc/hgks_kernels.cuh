@@ -5,9 +5,12 @@
 namespace hk {
 
 void launch_halo(double *Q, const Geo &g, cudaStream_t s);
+// split (mixed path, or null): a [2][5][pstride] FP32 buffer; when given, the
+// split state of Q is formed first (one more launch) and the FP32
+// reconstruction takes its differences from it
 template <typename R>
 void launch_recon(const double *Q, R *coef, unsigned char *flag, const Geo &g, const Scheme &S, Ctl *ctl,
-                  cudaStream_t s);
+                  cudaStream_t s, float *split = nullptr);
 template <typename R>
 void launch_flux(int axis, const R *coef, double *F, const Geo &g, const Scheme &S, Ctl *ctl, cudaStream_t s);
 void launch_update(int stage, double *Qn, double *Qs, double *Wacc, const double *Fx, const double *Fy,

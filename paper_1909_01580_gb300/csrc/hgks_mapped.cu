@@ -27,6 +27,8 @@ __global__ void __launch_bounds__(128) k_geom(double *__restrict__ geo, Geo g, M
         // flux kernels that follow
         ctl->mapS = Sf;
         ctl->mapC = m.moving ? cos(m.omega * ts) : 0.0;
+        ctl->mapAS = float(m.amp * Sf);
+        ctl->mapAUC = float(m.amp * m.omega * ctl->mapC);
     }
     double rec[NGEO];
     cell_geometry(m, i, j, k, Sf, rec);
@@ -69,7 +71,7 @@ __global__ void __launch_bounds__(128) k_flux_mapped(const R *__restrict__ coef,
                                                      MapGeo m, Scheme S, Ctl *ctl, int half)
 {
     if (!ctl->active) return;
-    flux_mapped_item<R, D>(coef, Fout, g, m, ctl->mapS, ctl->mapC, S, ctl->dt,
+    flux_mapped_item<R, D>(coef, Fout, g, m, ctl->mapS, ctl->mapC, ctl->mapAS, ctl->mapAUC, S, ctl->dt,
                            (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 

@@ -17,6 +17,10 @@ struct MapGeo {
     double amp, omega;
     int moving;
     const double *sx, *sy, *sz;
+    // FP32 copies for the mixed path's face geometry: lo, the reference
+    // spacing (hi - lo)/n, and the sine factors
+    float lof[3], hf[3];
+    const float *sxf, *syf, *szf;
 };
 
 // per-cell geometry record (FP64, over the padded cell box): volume,
@@ -893,9 +897,10 @@ __device__ __forceinline__ void eval_cell_mapped(const R *__restrict__ coef, con
 // precision.
 template <typename R, int D>
 __device__ __forceinline__ void flux_mapped_item(const R *__restrict__ coef, double *__restrict__ Fout, const Geo &g,
-                                                 const MapGeo &m, double Sf, double Cf, const Scheme &S, double dt,
-                                                 long long t)
+                                                 const MapGeo &m, double Sf, double Cf, float aSf, float aUCf,
+                                                 const Scheme &S, double dt, long long t)
 {
+    constexpr bool F32 = sizeof(R) == 4;  // mixed path: face geometry from the FP32 copies
     const int ex = g.nx + (D == 0), ey = g.ny + (D == 1);
     const long long nface = face_count<D>(g);
     long long face = t >> 2;
@@ -915,24 +920,34 @@ __device__ __forceinline__ void flux_mapped_item(const R *__restrict__ coef, dou
             int o[3] = {i, j, k};
             o[A] += sa;
             o[B] += sb;
-            const R sv = R(m.sx[o[0] + GHOST]) * R(m.sy[o[1] + GHOST]) * R(m.sz[o[2] + GHOST]);
+            R sv;
+            if constexpr (F32) sv = m.sxf[o[0] + GHOST] * m.syf[o[1] + GHOST] * m.szf[o[2] + GHOST];
+            else sv = R(m.sx[o[0] + GHOST]) * R(m.sy[o[1] + GHOST]) * R(m.sz[o[2] + GHOST]);
             const R qa = R(2 * sa - 1), qb = R(2 * sb - 1);
             sphi += R(0.25) * (R(1) + R(2) * qa * ea) * (R(1) + R(2) * qb * eb) * sv;
             spa += R(0.5) * qa * (R(1) + R(2) * qb * eb) * sv;
             spb += R(0.5) * qb * (R(1) + R(2) * qa * ea) * sv;
         }
-    const R aS = R(m.amp * Sf);
+    const R aS = F32 ? R(aSf) : R(m.amp * Sf);
     const R d = aS * sphi, dA = aS * spa, dB = aS * spb;
-    const R ug = m.moving ? R(m.amp * m.omega * Cf) * sphi : R(0);
+    const R ug = m.moving ? (F32 ? R(aUCf) : R(m.amp * m.omega * Cf)) * sphi : R(0);
     const int idx[3] = {i, j, k};
     R X[3], Xa[3], Xb[3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-        const double he = (m.hi[e] - m.lo[e]) / (double)m.n[e];
-        const double par = e == D ? 0.0 : (e == A ? 0.5 + (double)ea : 0.5 + (double)eb);
-        X[e] = R(m.lo[e] + ((double)idx[e] + par) * he) + d;
-        Xa[e] = (e == A ? R(he) : R(0)) + dA;
-        Xb[e] = (e == B ? R(he) : R(0)) + dB;
+        if constexpr (F32) {
+            const float he = m.hf[e];
+            const float par = e == D ? 0.0f : (e == A ? 0.5f + float(ea) : 0.5f + float(eb));
+            X[e] = R(m.lof[e] + (float(idx[e]) + par) * he) + d;
+            Xa[e] = (e == A ? R(he) : R(0)) + dA;
+            Xb[e] = (e == B ? R(he) : R(0)) + dB;
+        } else {
+            const double he = (m.hi[e] - m.lo[e]) / (double)m.n[e];
+            const double par = e == D ? 0.0 : (e == A ? 0.5 + (double)ea : 0.5 + (double)eb);
+            X[e] = R(m.lo[e] + ((double)idx[e] + par) * he) + d;
+            Xa[e] = (e == A ? R(he) : R(0)) + dA;
+            Xb[e] = (e == B ? R(he) : R(0)) + dB;
+        }
     }
     const R nrm[3] = {Xa[1] * Xb[2] - Xa[2] * Xb[1], Xa[2] * Xb[0] - Xa[0] * Xb[2], Xa[0] * Xb[1] - Xa[1] * Xb[0]};
     const R area = m_sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
