@@ -37,9 +37,12 @@ struct hgks {
     double *geo;                 // [NGEO][pstride] cell geometry at the stage time
     double *vol, *vnext;         // [ncell] volumes of the discrete conservation law
     double *sintab;              // sine factors of the map at the vertex indices
-    // mixed path on the uniform mesh: the split state Q_hi + Q_lo in FP32
-    // ([2][5][pstride]) that the reconstruction takes its differences from
+    // mixed path: the split state Q_hi + Q_lo in FP32 ([2][5][pstride]) that
+    // the reconstruction takes its differences from
     float *Qsplit;
+    // mixed path on a mapped mesh: FP32 copy of the cells' central second
+    // moments ([6][pstride]), written with the geometry
+    float *geof;
     // reconstruction in characteristic variables (option "characteristic")
     int charvar;
     void *coefc[3];              // per axis [2][50][nface_d] in the working precision
@@ -162,6 +165,7 @@ static void free_all(hgks_t *h)
         cudaFree(h->flagc[d]);
     }
     cudaFree(h->Qsplit);
+    cudaFree(h->geof);
 }
 
 extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, double Pr, const int bc[6], void *stream,
@@ -261,7 +265,7 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
         ok = cudaMalloc(ptrs[i], sizes[i]) == cudaSuccess;
         h->bytes += sizes[i];
     }
-    if (ok && !mapped && grid->precision == HGKS_MIXED) {
+    if (ok && grid->precision == HGKS_MIXED) {
         const size_t b = 2 * 5 * g.pstride * sizeof(float);
         ok = cudaMalloc((void **)&h->Qsplit, b) == cudaSuccess;
         h->bytes += b;
@@ -293,6 +297,12 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
         ok = ok && cudaMalloc((void **)&h->vol, g.ncell * sizeof(double)) == cudaSuccess;
         ok = ok && cudaMalloc((void **)&h->vnext, g.ncell * sizeof(double)) == cudaSuccess;
         h->bytes += tbytes + (hk::NGEO * g.pstride + 2 * g.ncell) * sizeof(double);
+        if (ok && grid->precision == HGKS_MIXED) {
+            ok = cudaMalloc((void **)&h->geof, 6 * g.pstride * sizeof(float)) == cudaSuccess;
+            h->bytes += 6 * g.pstride * sizeof(float);
+            h->map.geof = h->geof;
+            h->map.qsplit = h->Qsplit;
+        }
         for (int d = 0; d < 3; ++d) {
             h->map.lo[d] = grid->lo[d];
             h->map.hi[d] = grid->hi[d];
@@ -469,7 +479,8 @@ static int stage_fluxes_mapped(hgks_t *h, double *Q, int half, bool geom_ready)
     if (h->precision == HGKS_MIXED) {
         float *c = (float *)h->coef;
         {
-            PhaseTimer t(h, HGKS_PHASE_RECON, 2);
+            // split of Q (map.qsplit), reconstruction, positivity pass
+            PhaseTimer t(h, HGKS_PHASE_RECON, 3);
             hk::launch_recon_mapped<float>(Q, h->geo, c, h->flag, g, h->map, h->S, h->ctl, half, s);
         }
         PhaseTimer t(h, HGKS_PHASE_FLUX, 3);
@@ -483,8 +494,9 @@ static int stage_fluxes_mapped(hgks_t *h, double *Q, int half, bool geom_ready)
         PhaseTimer t(h, HGKS_PHASE_FLUX, 3);
         for (int d = 0; d < 3; ++d) hk::launch_flux_mapped<double>(d, c, h->F[d], g, h->map, h->S, h->ctl, half, s);
     }
-    // geometry, halo, reconstruction and its positivity pass, three face sweeps
-    return check_launch(h, geom_ready ? 6 : 7);
+    // geometry, halo, (mixed: split of Q,) reconstruction and its positivity
+    // pass, three face sweeps
+    return check_launch(h, (geom_ready ? 6 : 7) + (h->Qsplit ? 1 : 0));
 }
 
 static int stage_fluxes(hgks_t *h, double *Q, int half = 0, bool geom_ready = false)

@@ -34,6 +34,10 @@ __global__ void __launch_bounds__(128) k_geom(double *__restrict__ geo, Geo g, M
     cell_geometry(m, i, j, k, Sf, rec);
 #pragma unroll
     for (int e = 0; e < NGEO; ++e) geo[e * g.pstride + t] = rec[e];
+    if (m.geof) {
+#pragma unroll
+        for (int e = 0; e < 6; ++e) m.geof[e * g.pstride + t] = float(rec[4 + e]);
+    }
 }
 
 __global__ void k_vol_from_geo(const double *__restrict__ geo, double *__restrict__ vol, Geo g)
@@ -54,6 +58,13 @@ __global__ void __launch_bounds__(RM_BS) k_recon_mapped(const double *__restrict
     if (!ctl->active) return;
     recon_mapped_item<R>(Q, geo, coef, flag, g, m, ctl->mapS, S, ctl, stage + threadIdx.x,
                          (long long)blockIdx.x * RM_BS + threadIdx.x);
+}
+
+// split state Q = Q_hi + Q_lo of the stage's Q for the mixed reconstruction
+__global__ void k_split_mapped(const double *__restrict__ Q, float *__restrict__ hi, float *__restrict__ lo,
+                               long long n)
+{
+    split_item(Q, hi, lo, n, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 template <typename R>
@@ -147,6 +158,10 @@ template <typename R>
 void launch_recon_mapped(const double *Q, const double *geo, R *coef, unsigned char *flag, const Geo &g,
                          const MapGeo &m, const Scheme &S, Ctl *ctl, int half, cudaStream_t s)
 {
+    if (sizeof(R) == 4 && m.qsplit) {
+        const long long n = 5 * g.pstride;
+        k_split_mapped<<<nblk(n, 256), 256, 0, s>>>(Q, (float *)m.qsplit, (float *)m.qsplit + n, n);
+    }
     k_recon_mapped<R><<<nblk(g.cstride, RM_BS), RM_BS, 0, s>>>(Q, geo, coef, flag, g, m, S, ctl, half);
     k_positivity_mapped<R><<<nblk(g.cstride, 128), 128, 0, s>>>(Q, geo, coef, flag, g, m, S, ctl, half);
 }

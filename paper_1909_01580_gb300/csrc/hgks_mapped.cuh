@@ -21,6 +21,11 @@ struct MapGeo {
     // spacing (hi - lo)/n, and the sine factors
     float lof[3], hf[3];
     const float *sxf, *syf, *szf;
+    // mixed path (null otherwise): an FP32 copy of the cells' central second
+    // moments, [6][pstride], written by the geometry kernel, and the split
+    // state of the stage's Q (Q_hi + Q_lo in FP32, [2][5][pstride])
+    float *geof;
+    const float *qsplit;
 };
 
 // per-cell geometry record (FP64, over the padded cell box): volume,
@@ -434,7 +439,8 @@ __device__ __forceinline__ bool positivity_violated_mapped(const double *__restr
 // Per-cell staging for the reconstruction: the 18 neighbours' centroid
 // offsets in the scaled frame, (c_nb - c)/h, formed once in FP64 and kept in
 // shared memory in the working precision; in the mixed path also the 90
-// differences Q_nb - Q_c (formed in FP64).  Each thread owns one column of
+// differences Q_nb - Q_c, formed from the split state (hi_nb - hi_c) +
+// (lo_nb - lo_c) when the handle keeps one, else in FP64.  Each thread owns one column of
 // the block's array (stride RM_BS), so no synchronisation is needed.
 // ---------------------------------------------------------------------------
 constexpr int RM_BS = 64;  // threads per block of the reconstruction kernel
@@ -471,12 +477,23 @@ __device__ __forceinline__ int big_index(const int o[3])
 // the neighbour's second moments
 template <typename R>
 __device__ __forceinline__ void staged_row(const R *sh, const double *__restrict__ geo, const Geo &g, R ih2,
-                                           const R Mh[6], int s, long long pn, R row[9])
+                                           const R Mh[6], int s, long long pn, R row[9],
+                                           const float *__restrict__ geof = nullptr)
 {
     const R D0 = sh[(3 * s + 0) * RM_BS], D1 = sh[(3 * s + 1) * RM_BS], D2 = sh[(3 * s + 2) * RM_BS];
     R mm[6];
+    if constexpr (sizeof(R) == 4) {
+        if (geof) {
 #pragma unroll
-    for (int e = 0; e < 6; ++e) mm[e] = R(geo[(4 + e) * g.pstride + pn]) * ih2;
+            for (int e = 0; e < 6; ++e) mm[e] = geof[e * g.pstride + pn] * ih2;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 6; ++e) mm[e] = R(geo[(4 + e) * g.pstride + pn]) * ih2;
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < 6; ++e) mm[e] = R(geo[(4 + e) * g.pstride + pn]) * ih2;
+    }
     row[0] = D0;
     row[1] = D1;
     row[2] = D2;
@@ -626,6 +643,17 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
         qcd[v] = Q[v * g.pstride + pc];
         qcv[v] = R(qcd[v]);
     }
+    // the centre's split state (mixed path with a split copy of Q)
+    float hc[5] = {}, lc[5] = {};
+    if constexpr (RmStage<R>::dq) {
+        if (m.qsplit) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+                hc[v] = m.qsplit[v * g.pstride + pc];
+                lc[v] = m.qsplit[(5 + v) * g.pstride + pc];
+            }
+        }
+    }
     // stage the neighbours' scaled centroid offsets (and, mixed, the data
     // differences)
 #pragma unroll 1
@@ -636,8 +664,16 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
 #pragma unroll
         for (int d = 0; d < 3; ++d) sh[(3 * s + d) * RM_BS] = R((geo[(1 + d) * g.pstride + pn] - F.c[d]) * ih);
         if constexpr (RmStage<R>::dq) {
+            if (m.qsplit) {
+                // from the split state: (hi_nb - hi_c) + (lo_nb - lo_c)
 #pragma unroll
-            for (int v = 0; v < 5; ++v) sh[(54 + 18 * v + s) * RM_BS] = R(Q[v * g.pstride + pn] - qcd[v]);
+                for (int v = 0; v < 5; ++v)
+                    sh[(54 + 18 * v + s) * RM_BS] = (m.qsplit[v * g.pstride + pn] - hc[v]) +
+                                                     (m.qsplit[(5 + v) * g.pstride + pn] - lc[v]);
+            } else {
+#pragma unroll
+                for (int v = 0; v < 5; ++v) sh[(54 + 18 * v + s) * RM_BS] = R(Q[v * g.pstride + pn] - qcd[v]);
+            }
         }
     }
 
@@ -653,7 +689,7 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
             int o[3];
             big_offset_rt(s, o);
             R row[9];
-            staged_row<R>(sh, geo, g, ih2, Mh, s, pidx(g, i + o[0], j + o[1], k + o[2]), row);
+            staged_row<R>(sh, geo, g, ih2, Mh, s, pidx(g, i + o[0], j + o[1], k + o[2]), row, m.geof);
 #pragma unroll
             for (int a = 0; a < 9; ++a)
 #pragma unroll
@@ -672,7 +708,7 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
                 big_offset_rt(s, o);
                 const long long pn = pidx(g, i + o[0], j + o[1], k + o[2]);
                 R row[9];
-                staged_row<R>(sh, geo, g, ih2, Mh, s, pn, row);
+                staged_row<R>(sh, geo, g, ih2, Mh, s, pn, row, m.geof);
                 const R dq = staged_dq<R>(sh, Q, g, v, s, pn, qc);
 #pragma unroll
                 for (int n = 0; n < 9; ++n) a[n] += row[n] * dq;
