@@ -1070,9 +1070,17 @@ __device__ __forceinline__ void flux_mapped_item(const R *__restrict__ coef, dou
         f[q] += __shfl_xor_sync(0xffffffffu, f[q], 1);
         f[q] += __shfl_xor_sync(0xffffffffu, f[q], 2);
     }
-    if (valid && gp == 0) {
+    // lane gp stores the sums q = gp, gp + 4, gp + 8, so the FP64
+    // conversions are spread over the face's 4 lanes
+    static_assert(NFACE_M == 11, "the selection below covers 11 sums");
+    if (valid) {
+        const bool b0 = gp & 1, b1 = gp & 2;
 #pragma unroll
-        for (int q = 0; q < NFACE_M; ++q) Fout[q * nface + face] = double(f[q]);
+        for (int r = 0; r < 2; ++r) {
+            const R v = b1 ? (b0 ? f[4 * r + 3] : f[4 * r + 2]) : (b0 ? f[4 * r + 1] : f[4 * r]);
+            Fout[(gp + 4 * r) * nface + face] = double(v);
+        }
+        if (gp < 3) Fout[(gp + 8) * nface + face] = double(b1 ? f[10] : (b0 ? f[9] : f[8]));
     }
 }
 
