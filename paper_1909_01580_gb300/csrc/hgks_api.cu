@@ -307,6 +307,8 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
             h->map.lo[d] = grid->lo[d];
             h->map.hi[d] = grid->hi[d];
             h->map.n[d] = grid->n[d];
+            h->map.h[d] = (grid->hi[d] - grid->lo[d]) / (double)grid->n[d];
+            h->map.ih[d] = 1.0 / h->map.h[d];
         }
         h->map.amp = grid->mesh_amp;
         h->map.omega = grid->mesh_omega;

@@ -14,6 +14,7 @@ namespace hk {
 struct MapGeo {
     double lo[3], hi[3];
     int n[3];
+    double h[3], ih[3];  // reference spacing (hi - lo)/n and its inverse
     double amp, omega;
     int moving;
     const double *sx, *sy, *sz;
@@ -70,7 +71,7 @@ HK_HD void cell_geometry(const MapGeo &m, int i, int j, int k, double S, double 
     double h[3], xc[3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
-        h[e] = (m.hi[e] - m.lo[e]) / (double)m.n[e];
+        h[e] = m.h[e];
         xc[e] = m.lo[e] + ((double)idx[e] + 0.5) * h[e];
     }
     const double aS = m.amp * S;
@@ -98,13 +99,14 @@ HK_HD void cell_geometry(const MapGeo &m, int i, int j, int k, double S, double 
             gD[2] += f0 * f1 * s2 * sv[v];
         }
         D *= aS;
-        const double det = hprod * (1.0 + aS * (gD[0] / h[0] + gD[1] / h[1] + gD[2] / h[2]));
+        const double det = hprod * (1.0 + aS * (gD[0] * m.ih[0] + gD[1] * m.ih[1] + gD[2] * m.ih[2]));
         w[q] = 0.125 * fabs(det);
         for (int d = 0; d < 3; ++d) Y[q][d] = p[d] * h[d] + D;
         vol += w[q];
         for (int d = 0; d < 3; ++d) m1[d] += w[q] * Y[q][d];
     }
-    const double cy[3] = {m1[0] / vol, m1[1] / vol, m1[2] / vol};
+    const double ivol = 1.0 / vol;
+    const double cy[3] = {m1[0] * ivol, m1[1] * ivol, m1[2] * ivol};
     double M[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
@@ -118,7 +120,7 @@ HK_HD void cell_geometry(const MapGeo &m, int i, int j, int k, double S, double 
     }
     out[0] = vol;
     for (int d = 0; d < 3; ++d) out[1 + d] = xc[d] + cy[d];
-    for (int e = 0; e < 6; ++e) out[4 + e] = M[e] / vol;
+    for (int e = 0; e < 6; ++e) out[4 + e] = M[e] * ivol;
 }
 
 // ---------------------------------------------------------------------------
@@ -794,7 +796,7 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
         R x0[3], hr[3];
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
-            const double he = (m.hi[e] - m.lo[e]) / (double)m.n[e];
+            const double he = m.h[e];
             x0[e] = R((m.lo[e] + ((double)idx[e] + 0.5) * he - F.c[e]) * ih);
             hr[e] = R(he * ih);
         }
@@ -978,7 +980,7 @@ __device__ __forceinline__ void flux_mapped_item(const R *__restrict__ coef, dou
             Xa[e] = (e == A ? R(he) : R(0)) + dA;
             Xb[e] = (e == B ? R(he) : R(0)) + dB;
         } else {
-            const double he = (m.hi[e] - m.lo[e]) / (double)m.n[e];
+            const double he = m.h[e];
             const double par = e == D ? 0.0 : (e == A ? 0.5 + (double)ea : 0.5 + (double)eb);
             X[e] = R(m.lo[e] + ((double)idx[e] + par) * he) + d;
             Xa[e] = (e == A ? R(he) : R(0)) + dA;
