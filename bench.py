@@ -42,8 +42,8 @@ UNIT = "cell-stage updates/s"
 # capture, scaled by the faces of a 128^3 launch (traffic grows with the
 # cells: the coefficient array is read once).
 FLUX_FP64_FLOP_PER_GP = 3042.0
-FLUX_FP32_FLOP_PER_GP = 2845.0
-FLUX_TRAFFIC_BYTES_PER_FACE = {"fp64": 14.306e6 / 33792, "mixed": 7.215e6 / 33792}
+FLUX_FP32_FLOP_PER_GP = 2803.0
+FLUX_TRAFFIC_BYTES_PER_FACE = {"fp64": 14.306e6 / 33792, "mixed": 7.212e6 / 33792}
 # GB300 ALU peaks derived from unit counts and clocks: 152 SMs x 2070 MHz x
 # (FP64: 2 DFMA/clk/SM = 4 flop; FP32: 128 FMA/clk/SM = 256 flop).
 SM_COUNT = 152

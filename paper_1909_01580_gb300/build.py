@@ -17,8 +17,11 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhgks.so")
 SOURCES = ["hgks_kernels.cu", "hgks_mapped.cu", "hgks_char.cu", "hgks_api.cu", "hgks_noalloc.cu", "hgks_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# -prec-div=false / -prec-sqrt=false: FP32 division and square root of the
+# mixed path to within 2 ulp instead of correctly rounded (FP64 arithmetic is
+# unaffected); 5% on the mixed TGV step, 8% on the mixed moving-mesh step
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              "--expt-relaxed-constexpr"]
+              "--expt-relaxed-constexpr", "-prec-div=false", "-prec-sqrt=false"]
 
 
 def _nvcc() -> str:
