@@ -759,6 +759,55 @@ template <typename R> HK_HD void sub_stencil_sp_rt(const Stencil<R> &st, int m, 
     }
 }
 
+// One-pass form of the WENO-AO combination (Sec. 2, eqs. (para) and
+// (nonlinear)).  With x_m = 1/(beta_m + eps), y0 = 1/(beta0 + eps), the
+// exponent p of tau/(beta + eps) and t = tau^p, the weights are
+// w_m = g_m (1 + t x_m^p) and w_0 = g_0 (1 + t y0^p), so the coefficient of
+// P_m in P~ = (w0/g0) P0 + sum (w_m - w0 g_m/g0) P_m (before normalising by
+// the weight sum) is
+//   g_m t (x_m^p - y0^p) = g_m t y0 (beta0 - beta_m) x_m k_m,
+// k_m = 1 (p = 1) or x_m + y0 (p = 2), and the weight sum is
+// w_0 + g_m (n + t sum x_m^p).  Both are linear in t, so a single pass over
+// the n sub-stencils gathers every sum before tau is known; the difference
+// beta0 - beta_m that tau needs also carries the coefficients, so no
+// cancellation between nearly equal weights enters them.
+template <typename R> struct AoSums {
+    R y0, dsum, xs, T[3];
+    bool pow2;
+    HK_HD void init(R beta0, R eps, bool p2)
+    {
+        y0 = R(1) / (beta0 + eps);
+        dsum = xs = T[0] = T[1] = T[2] = R(0);
+        pow2 = p2;
+    }
+    // linear polynomial with coefficients b (indicator |b|^2)
+    HK_HD void add(R beta0, R eps, const R b[3])
+    {
+        const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+        const R d = beta0 - bm;
+        dsum += m_abs(d);
+        const R x = R(1) / (bm + eps);
+        xs += pow2 ? x * x : x;
+        const R f = d * x * (pow2 ? x + y0 : R(1));
+        T[0] += f * b[0];
+        T[1] += f * b[1];
+        T[2] += f * b[2];
+    }
+    // P~ - Q_c = iw (f0 (P0 - Q_c) + lin . X) for NSUB sub-stencils with
+    // linear weights g0 and gm each
+    template <int NSUB> HK_HD void combine(R g0, R gm, R &iw, R &f0, R lin[3]) const
+    {
+        const R tau = dsum * R(1.0 / NSUB);
+        const R t = pow2 ? tau * tau : tau;
+        f0 = R(1) + t * (pow2 ? y0 * y0 : y0);
+        iw = R(1) / (g0 * f0 + gm * (R(NSUB) + t * xs));
+        const R cl = gm * t * y0;
+        lin[0] = cl * T[0];
+        lin[1] = cl * T[1];
+        lin[2] = cl * T[2];
+    }
+};
+
 // WENO-AO combination for one conserved variable (Sec. 2): P0, the 24
 // linear P_m, their indicators, tau of eq. (para), the nonlinear weights of
 // eq. (nonlinear) and P~ = (w0/g0) P0 + sum (w_m - w0 g_m/g0) P_m, returned
@@ -768,47 +817,24 @@ template <typename R>
 HK_HD void weno_ao(const Stencil<R> &st, const Scheme &S, R out[9], R &rad)
 {
     const R g0 = R(1.0 - 24.0 * S.Gamma_lin), gm = R(S.Gamma_lin), eps = R(S.weno_eps);
-    const R ig0 = R(1) / g0;
     R a[9];
     big_stencil_P0(st, a);
     const R beta0 = beta_quadratic(a);
     R r = bound_quadratic(a);
-    // pass 1: indicators of the 24 linear polynomials and tau
-    R tau = R(0);
-#define HK_PASS1(M)                                                   \
+    AoSums<R> acc;
+    acc.init(beta0, eps, S.weno_pow == 2);
+#define HK_PASS(M)                                                    \
     {                                                                 \
         R b[3];                                                       \
         sub_stencil<M>(st, b);                                        \
-        const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];         \
-        tau += m_abs(beta0 - bm);                                     \
+        acc.add(beta0, eps, b);                                       \
         r = m_max(r, bound_linear(b));                                \
     }
-    HK_FOR_SUBSTENCILS(HK_PASS1)
-#undef HK_PASS1
-    tau *= R(1.0 / 24.0);
+    HK_FOR_SUBSTENCILS(HK_PASS)
+#undef HK_PASS
     rad = r;
-    // pass 2: weights and the combination, normalised at the end
-    const R x0 = tau / (beta0 + eps);
-    const R w0 = g0 * (R(1) + (S.weno_pow == 2 ? x0 * x0 : x0));
-    R wsum = w0;
-    R lin[3] = {R(0), R(0), R(0)};
-#define HK_PASS2(M)                                                   \
-    {                                                                 \
-        R b[3];                                                       \
-        sub_stencil<M>(st, b);                                        \
-        const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];         \
-        const R xm = tau / (bm + eps);                                \
-        const R wm = gm * (R(1) + (S.weno_pow == 2 ? xm * xm : xm));  \
-        wsum += wm;                                                   \
-        const R cm = wm - w0 * gm * ig0;                              \
-        lin[0] += cm * b[0];                                          \
-        lin[1] += cm * b[1];                                          \
-        lin[2] += cm * b[2];                                          \
-    }
-    HK_FOR_SUBSTENCILS(HK_PASS2)
-#undef HK_PASS2
-    const R iw = R(1) / wsum;
-    const R f0 = w0 * ig0;
+    R iw, f0, lin[3];
+    acc.template combine<24>(g0, gm, iw, f0, lin);
 #pragma unroll
     for (int n = 0; n < 9; ++n) out[n] = iw * (f0 * a[n] + (n < 3 ? lin[n] : R(0)));
 }
@@ -820,45 +846,24 @@ template <typename R>
 HK_HD void weno_ao_sp(const Stencil<R> &st, const Scheme &S, R out[9], R &rad)
 {
     const R g0 = R(1.0 - 8.0 * S.Gamma_lin), gm = R(S.Gamma_lin), eps = R(S.weno_eps);
-    const R ig0 = R(1) / g0;
     R a[9];
     big_stencil_P0_sp(st, a);
     const R beta0 = beta_quadratic(a);
     R r = bound_quadratic(a);
-    R tau = R(0);
-#define HK_PASS1_SP(M)                                                \
+    AoSums<R> acc;
+    acc.init(beta0, eps, S.weno_pow == 2);
+#define HK_PASS_SP(M)                                                 \
     {                                                                 \
         R b[3];                                                       \
         sub_stencil_sp<M>(st, b);                                     \
-        const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];         \
-        tau += m_abs(beta0 - bm);                                     \
+        acc.add(beta0, eps, b);                                       \
         r = m_max(r, bound_linear(b));                                \
     }
-    HK_FOR_SUBSTENCILS_SP(HK_PASS1_SP)
-#undef HK_PASS1_SP
-    tau *= R(1.0 / 8.0);
+    HK_FOR_SUBSTENCILS_SP(HK_PASS_SP)
+#undef HK_PASS_SP
     rad = r;
-    const R x0 = tau / (beta0 + eps);
-    const R w0 = g0 * (R(1) + (S.weno_pow == 2 ? x0 * x0 : x0));
-    R wsum = w0;
-    R lin[3] = {R(0), R(0), R(0)};
-#define HK_PASS2_SP(M)                                                \
-    {                                                                 \
-        R b[3];                                                       \
-        sub_stencil_sp<M>(st, b);                                     \
-        const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];         \
-        const R xm = tau / (bm + eps);                                \
-        const R wm = gm * (R(1) + (S.weno_pow == 2 ? xm * xm : xm));  \
-        wsum += wm;                                                   \
-        const R cm = wm - w0 * gm * ig0;                              \
-        lin[0] += cm * b[0];                                          \
-        lin[1] += cm * b[1];                                          \
-        lin[2] += cm * b[2];                                          \
-    }
-    HK_FOR_SUBSTENCILS_SP(HK_PASS2_SP)
-#undef HK_PASS2_SP
-    const R iw = R(1) / wsum;
-    const R f0 = w0 * ig0;
+    R iw, f0, lin[3];
+    acc.template combine<8>(g0, gm, iw, f0, lin);
 #pragma unroll
     for (int n = 0; n < 9; ++n) out[n] = iw * (f0 * a[n] + (n < 3 ? lin[n] : R(0)));
 }

@@ -80,24 +80,40 @@ HK_HD void cell_geometry(const MapGeo &m, int i, int j, int k, double S, double 
     for (int q = 0; q < 8; ++q)
         sv[q] = m.sx[i + (q & 1) + GHOST] * m.sy[j + ((q >> 1) & 1) + GHOST] * m.sz[k + (q >> 2) + GHOST];
     const double hprod = h[0] * h[1] * h[2];
+    // D and its p-gradient at the 2x2x2 Gauss points, one axis at a time: at
+    // the point index ia (p = -g, +g) vertex 0 of the axis weighs 1/2 - p and
+    // vertex 1 weighs 1/2 + p; a derivative along an axis is the difference
+    // of its two vertex values, constant along that axis.
+    const double wv[2][2] = {{0.5 + GAUSS_S, 0.5 - GAUSS_S}, {0.5 - GAUSS_S, 0.5 + GAUSS_S}};
+    double ax[2][4], dax[4];  // along x: [ix][b + 2c], and d/dp_x at [b + 2c]
+#pragma unroll
+    for (int yz = 0; yz < 4; ++yz) {
+        const double v0 = sv[2 * yz], v1 = sv[2 * yz + 1];
+        dax[yz] = v1 - v0;
+#pragma unroll
+        for (int ix = 0; ix < 2; ++ix) ax[ix][yz] = v0 * wv[ix][0] + v1 * wv[ix][1];
+    }
+    double axy[2][2][2], dxy[2][2], dyx[2][2];  // [ix][iy][c], d/dp_x at [iy][c], d/dp_y at [ix][c]
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+#pragma unroll
+        for (int iy = 0; iy < 2; ++iy) {
+#pragma unroll
+            for (int ix = 0; ix < 2; ++ix)
+                axy[ix][iy][c] = ax[ix][2 * c] * wv[iy][0] + ax[ix][2 * c + 1] * wv[iy][1];
+            dxy[iy][c] = dax[2 * c] * wv[iy][0] + dax[2 * c + 1] * wv[iy][1];
+        }
+#pragma unroll
+        for (int ix = 0; ix < 2; ++ix) dyx[ix][c] = ax[ix][2 * c + 1] - ax[ix][2 * c];
+    }
     double Y[8][3], w[8], vol = 0.0, m1[3] = {0, 0, 0};
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        const double p[3] = {(q & 1) ? GAUSS_S : -GAUSS_S, ((q >> 1) & 1) ? GAUSS_S : -GAUSS_S,
-                             (q >> 2) ? GAUSS_S : -GAUSS_S};
-        const double lo[3] = {0.5 - p[0], 0.5 - p[1], 0.5 - p[2]};
-        const double hi[3] = {0.5 + p[0], 0.5 + p[1], 0.5 + p[2]};
-        double D = 0.0, gD[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-        for (int v = 0; v < 8; ++v) {
-            const int a = v & 1, b = (v >> 1) & 1, c = v >> 2;
-            const double f0 = a ? hi[0] : lo[0], f1 = b ? hi[1] : lo[1], f2 = c ? hi[2] : lo[2];
-            const double s0 = a ? 1.0 : -1.0, s1 = b ? 1.0 : -1.0, s2 = c ? 1.0 : -1.0;
-            D += f0 * f1 * f2 * sv[v];
-            gD[0] += s0 * f1 * f2 * sv[v];
-            gD[1] += f0 * s1 * f2 * sv[v];
-            gD[2] += f0 * f1 * s2 * sv[v];
-        }
+        const int ix = q & 1, iy = (q >> 1) & 1, iz = q >> 2;
+        const double p[3] = {ix ? GAUSS_S : -GAUSS_S, iy ? GAUSS_S : -GAUSS_S, iz ? GAUSS_S : -GAUSS_S};
+        double D = axy[ix][iy][0] * wv[iz][0] + axy[ix][iy][1] * wv[iz][1];
+        const double gD[3] = {dxy[iy][0] * wv[iz][0] + dxy[iy][1] * wv[iz][1],
+                              dyx[ix][0] * wv[iz][0] + dyx[ix][1] * wv[iz][1], axy[ix][iy][1] - axy[ix][iy][0]};
         D *= aS;
         const double det = hprod * (1.0 + aS * (gD[0] * m.ih[0] + gD[1] * m.ih[1] + gD[2] * m.ih[2]));
         w[q] = 0.125 * fabs(det);
@@ -635,7 +651,6 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
     const R ih2 = R(ih * ih);
     const R Mh[6] = {R(F.Mh[0]), R(F.Mh[1]), R(F.Mh[2]), R(F.Mh[3]), R(F.Mh[4]), R(F.Mh[5])};
     const R g0 = R(1.0 - 24.0 * Sch.Gamma_lin), gm = R(Sch.Gamma_lin), eps = R(Sch.weno_eps);
-    const R ig0 = R(1) / g0;
     const bool pow2 = Sch.weno_pow == 2;
     const long long pc = pidx(g, i, j, k);
     double qcd[5];
@@ -724,38 +739,15 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
     R beta0[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) beta0[v] = coef[coef_slot(v, 0) * g.cstride + t];
-    // sub-stencils, first pass: tau = mean |beta0 - beta_m| and the largest
+    // one pass over the sub-stencils (AoSums): the sums of the nonlinear
+    // weights and of the linear part of P~, and the largest
     // |b_x| + |b_y| + |b_z| over the P_m (positivity bound)
-    R tau[5], bsum[5];
-#pragma unroll
-    for (int v = 0; v < 5; ++v) tau[v] = bsum[v] = R(0);
-#pragma unroll 1
-    for (int M = 0; M < 24; ++M) {
-        int o[4][3];
-        sub_offsets_rt(M, o);
-        R P[3][4];
-        sub_pinv<R>(sh, o, P);
-#pragma unroll
-        for (int v = 0; v < 5; ++v) {
-            R dq[4];
-            sub_dq<R>(sh, Q, g, v, i, j, k, qcd[v], o, dq);
-            R b[3];
-#pragma unroll
-            for (int d = 0; d < 3; ++d) b[d] = P[d][0] * dq[0] + P[d][1] * dq[1] + P[d][2] * dq[2] + P[d][3] * dq[3];
-            const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
-            tau[v] += m_abs(beta0[v] - bm);
-            bsum[v] = m_max(bsum[v], m_abs(b[0]) + m_abs(b[1]) + m_abs(b[2]));
-        }
-    }
-    // second pass: nonlinear weights and the linear part of P~
-    R w0[5], wsum[5], lin[5][3];
+    AoSums<R> acc[5];
+    R bsum[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-        tau[v] *= R(1.0 / 24.0);
-        const R x0 = tau[v] / (beta0[v] + eps);
-        w0[v] = g0 * (R(1) + (pow2 ? x0 * x0 : x0));
-        wsum[v] = w0[v];
-        lin[v][0] = lin[v][1] = lin[v][2] = R(0);
+        acc[v].init(beta0[v], eps, pow2);
+        bsum[v] = R(0);
     }
 #pragma unroll 1
     for (int M = 0; M < 24; ++M) {
@@ -770,14 +762,8 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
             R b[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) b[d] = P[d][0] * dq[0] + P[d][1] * dq[1] + P[d][2] * dq[2] + P[d][3] * dq[3];
-            const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
-            const R xm = tau[v] / (bm + eps);
-            const R wm = gm * (R(1) + (pow2 ? xm * xm : xm));
-            wsum[v] += wm;
-            const R cm = wm - w0[v] * gm * ig0;
-            lin[v][0] += cm * b[0];
-            lin[v][1] += cm * b[1];
-            lin[v][2] += cm * b[2];
+            acc[v].add(beta0[v], eps, b);
+            bsum[v] = m_max(bsum[v], m_abs(b[0]) + m_abs(b[1]) + m_abs(b[2]));
         }
     }
     // extents of X and of the monomials over the cell's 24 face Gauss
@@ -837,8 +823,8 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
     R rad[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-        const R iw = R(1) / wsum[v];
-        const R f0 = w0[v] * ig0;
+        R iw, f0, lin[3];
+        acc[v].template combine<24>(g0, gm, iw, f0, lin);
         coef[coef_slot(v, 0) * g.cstride + t] = qcv[v];
         R r0 = R(0);
 #pragma unroll
@@ -846,7 +832,7 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
             R *cp = coef + coef_slot(v, 1 + n) * g.cstride + t;
             const R a = *cp;
             r0 += m_abs(a) * ext[n];
-            *cp = iw * (f0 * a + (n < 3 ? lin[v][n] : R(0)));
+            *cp = iw * (f0 * a + (n < 3 ? lin[n] : R(0)));
         }
         // bound of |P_m - Q_c| at the Gauss points for all 25 P_m
         rad[v] = m_max(r0, bsum[v] * xmax) * R(1.0000001);
