@@ -780,18 +780,22 @@ template <typename R> struct AoSums {
         dsum = xs = T[0] = T[1] = T[2] = R(0);
         pow2 = p2;
     }
-    // linear polynomial with coefficients b (indicator |b|^2)
-    HK_HD void add(R beta0, R eps, const R b[3])
+    // linear polynomial with coefficients b (indicator bm = |b|^2), given
+    // x = 1/(bm + eps)
+    HK_HD void add_x(R beta0, const R b[3], R bm, R x)
     {
-        const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
         const R d = beta0 - bm;
         dsum += m_abs(d);
-        const R x = R(1) / (bm + eps);
         xs += pow2 ? x * x : x;
         const R f = d * x * (pow2 ? x + y0 : R(1));
         T[0] += f * b[0];
         T[1] += f * b[1];
         T[2] += f * b[2];
+    }
+    HK_HD void add(R beta0, R eps, const R b[3])
+    {
+        const R bm = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+        add_x(beta0, b, bm, R(1) / (bm + eps));
     }
     // P~ - Q_c = iw (f0 (P0 - Q_c) + lin . X) for NSUB sub-stencils with
     // linear weights g0 and gm each
@@ -808,6 +812,30 @@ template <typename R> struct AoSums {
     }
 };
 
+// x_q = 1/d_q for four nonzero d_q.  In FP64, where a division costs
+// several FP64-pipe operations, one division of the product and nine
+// multiplications; in other precisions four divisions.
+template <typename R> HK_HD void recip4(const R d[4], R x[4])
+{
+    if constexpr (sizeof(R) == 8) {
+        const R p01 = d[0] * d[1], p23 = d[2] * d[3];
+        const R r = R(1) / (p01 * p23);
+        const R r01 = r * p23, r23 = r * p01;
+        x[0] = r01 * d[1];
+        x[1] = r01 * d[0];
+        x[2] = r23 * d[3];
+        x[3] = r23 * d[2];
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = R(1) / d[q];
+    }
+}
+
+// the sub-stencils in groups of four (m = 0..23 and the 8 of S')
+#define HK_FOR_SUBSTENCIL_QUADS(X) X(0, 1, 2, 3) X(4, 5, 6, 7) X(8, 9, 10, 11) X(12, 13, 14, 15) \
+    X(16, 17, 18, 19) X(20, 21, 22, 23)
+#define HK_FOR_SUBSTENCIL_QUADS_SP(X) X(0, 1, 2, 3) X(4, 5, 6, 7)
+
 // WENO-AO combination for one conserved variable (Sec. 2): P0, the 24
 // linear P_m, their indicators, tau of eq. (para), the nonlinear weights of
 // eq. (nonlinear) and P~ = (w0/g0) P0 + sum (w_m - w0 g_m/g0) P_m, returned
@@ -823,14 +851,22 @@ HK_HD void weno_ao(const Stencil<R> &st, const Scheme &S, R out[9], R &rad)
     R r = bound_quadratic(a);
     AoSums<R> acc;
     acc.init(beta0, eps, S.weno_pow == 2);
-#define HK_PASS(M)                                                    \
-    {                                                                 \
-        R b[3];                                                       \
-        sub_stencil<M>(st, b);                                        \
-        acc.add(beta0, eps, b);                                       \
-        r = m_max(r, bound_linear(b));                                \
+#define HK_PASS(M0, M1, M2, M3)                                                \
+    {                                                                          \
+        R b[4][3], bm[4], den[4], x[4];                                        \
+        sub_stencil<M0>(st, b[0]);                                             \
+        sub_stencil<M1>(st, b[1]);                                             \
+        sub_stencil<M2>(st, b[2]);                                             \
+        sub_stencil<M3>(st, b[3]);                                             \
+        for (int q = 0; q < 4; ++q) {                                          \
+            bm[q] = b[q][0] * b[q][0] + b[q][1] * b[q][1] + b[q][2] * b[q][2]; \
+            den[q] = bm[q] + eps;                                              \
+            r = m_max(r, bound_linear(b[q]));                                  \
+        }                                                                      \
+        recip4(den, x);                                                        \
+        for (int q = 0; q < 4; ++q) acc.add_x(beta0, b[q], bm[q], x[q]);      \
     }
-    HK_FOR_SUBSTENCILS(HK_PASS)
+    HK_FOR_SUBSTENCIL_QUADS(HK_PASS)
 #undef HK_PASS
     rad = r;
     R iw, f0, lin[3];
@@ -852,14 +888,22 @@ HK_HD void weno_ao_sp(const Stencil<R> &st, const Scheme &S, R out[9], R &rad)
     R r = bound_quadratic(a);
     AoSums<R> acc;
     acc.init(beta0, eps, S.weno_pow == 2);
-#define HK_PASS_SP(M)                                                 \
-    {                                                                 \
-        R b[3];                                                       \
-        sub_stencil_sp<M>(st, b);                                     \
-        acc.add(beta0, eps, b);                                       \
-        r = m_max(r, bound_linear(b));                                \
+#define HK_PASS_SP(M0, M1, M2, M3)                                             \
+    {                                                                          \
+        R b[4][3], bm[4], den[4], x[4];                                        \
+        sub_stencil_sp<M0>(st, b[0]);                                          \
+        sub_stencil_sp<M1>(st, b[1]);                                          \
+        sub_stencil_sp<M2>(st, b[2]);                                          \
+        sub_stencil_sp<M3>(st, b[3]);                                          \
+        for (int q = 0; q < 4; ++q) {                                          \
+            bm[q] = b[q][0] * b[q][0] + b[q][1] * b[q][1] + b[q][2] * b[q][2]; \
+            den[q] = bm[q] + eps;                                              \
+            r = m_max(r, bound_linear(b[q]));                                  \
+        }                                                                      \
+        recip4(den, x);                                                        \
+        for (int q = 0; q < 4; ++q) acc.add_x(beta0, b[q], bm[q], x[q]);      \
     }
-    HK_FOR_SUBSTENCILS_SP(HK_PASS_SP)
+    HK_FOR_SUBSTENCIL_QUADS_SP(HK_PASS_SP)
 #undef HK_PASS_SP
     rad = r;
     R iw, f0, lin[3];
