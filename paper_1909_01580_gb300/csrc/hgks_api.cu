@@ -323,6 +323,7 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
         for (int d = 0; d < 3; ++d) {
             h->map.lof[d] = float(grid->lo[d]);
             h->map.hf[d] = float((grid->hi[d] - grid->lo[d]) / grid->n[d]);
+            h->map.ihf[d] = float(grid->n[d] / (grid->hi[d] - grid->lo[d]));
         }
     }
     ok = ok && cudaMalloc((void **)&h->ctl, sizeof(Ctl)) == cudaSuccess;
@@ -571,7 +572,7 @@ extern "C" int hgks_step(hgks_t *h, int nsteps, double cfl, double dt_fixed, dou
                 if (h->mesh != 0) {
                     // h = |Omega|^(1/3) of the mesh at t_n
                     hk::launch_geom(h->geo, g, h->map, h->ctl, 0, 0.0, s);
-                    hk::launch_cfl_mapped(h->Qn, h->geo, g, h->S.gamma, h->ctl, s);
+                    hk::launch_cfl_mapped(h->Qn, h->geo, g, h->S.gamma, h->ctl, s, h->precision == HGKS_MIXED);
                     ++nl;
                 } else {
                     hk::launch_cfl(h->Qn, g, h->S.gamma, h->ctl, s, h->precision == HGKS_MIXED);

@@ -9,7 +9,8 @@ namespace hk {
 __device__ __forceinline__ double stage_time(const Ctl *ctl, int half) { return ctl->t + (half ? 0.5 * ctl->dt : 0.0); }
 
 // geometry of every cell of the padded box at the stage time (or at t_fixed
-// when ctl is null)
+// when ctl is null); MIXED: the small quantities in FP32 (cell_geometry_mixed)
+template <bool MIXED>
 __global__ void __launch_bounds__(128) k_geom(double *__restrict__ geo, Geo g, MapGeo m, Ctl *ctl, int half,
                                               double t_fixed)
 {
@@ -31,13 +32,20 @@ __global__ void __launch_bounds__(128) k_geom(double *__restrict__ geo, Geo g, M
         ctl->mapAUC = float(m.amp * m.omega * ctl->mapC);
     }
     double rec[NGEO];
-    cell_geometry(m, i, j, k, Sf, rec);
+    if constexpr (MIXED) {
+        float fm[6];
+        cell_geometry_mixed(m, i, j, k, float(m.amp * Sf), rec, fm);
+#pragma unroll
+        for (int e = 0; e < 6; ++e) m.geof[e * g.pstride + t] = fm[e];
+    } else {
+        cell_geometry(m, i, j, k, Sf, rec);
+        if (m.geof) {
+#pragma unroll
+            for (int e = 0; e < 6; ++e) m.geof[e * g.pstride + t] = float(rec[4 + e]);
+        }
+    }
 #pragma unroll
     for (int e = 0; e < NGEO; ++e) geo[e * g.pstride + t] = rec[e];
-    if (m.geof) {
-#pragma unroll
-        for (int e = 0; e < 6; ++e) m.geof[e * g.pstride + t] = float(rec[4 + e]);
-    }
 }
 
 __global__ void k_vol_from_geo(const double *__restrict__ geo, double *__restrict__ vol, Geo g)
@@ -117,13 +125,33 @@ __global__ void k_residual_mapped(const double *__restrict__ Fx, const double *_
     }
 }
 
-// CFL with h = |Omega|^(1/3) of the geometry at t_n
+// CFL with h = |Omega|^(1/3) of the geometry at t_n; MIXED: FP32
+// candidates (FP64 minimum), a cell whose FP32 pressure is not clearly
+// positive recomputed in FP64
+template <bool MIXED>
 __global__ void __launch_bounds__(256) k_cfl_mapped(const double *__restrict__ Q, const double *__restrict__ geo,
                                                     Geo g, double gamma, Ctl *ctl)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double v = INFINITY;
-    if (t < g.ncell) {
+    bool done = false;
+    if (MIXED && t < g.ncell) {
+        int i, j, k;
+        split3(t, g.nx, g.ny, i, j, k);
+        const long long pi = pidx(g, i, j, k);
+        float W[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) W[q] = float(Q[q * g.pstride + pi]);
+        const float ir = 1.0f / W[0];
+        const float m2 = W[1] * W[1] + W[2] * W[2] + W[3] * W[3];
+        const float p = float(gamma - 1.0) * (W[4] - 0.5f * m2 * ir);
+        if (W[0] > 0.0f && p > 1e-4f * W[4]) {
+            const float s = sqrtf(m2) * ir + sqrtf(float(gamma) * p * ir);
+            v = double(cbrtf(float(geo[pi])) / s);
+            done = true;
+        }
+    }
+    if (!done && t < g.ncell) {
         int i, j, k;
         split3(t, g.nx, g.ny, i, j, k);
         const long long pi = pidx(g, i, j, k);
@@ -146,7 +174,10 @@ static inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1
 void launch_geom(double *geo, const Geo &g, const MapGeo &m, Ctl *ctl, int half, double t_fixed,
                  cudaStream_t s)
 {
-    k_geom<<<nblk(g.pstride, 128), 128, 0, s>>>(geo, g, m, ctl, half, t_fixed);
+    // a mixed handle's stage geometry in FP32 arithmetic; the FP64 geometry
+    // for FP64 handles and for the initial volumes (ctl null)
+    if (m.geof && ctl) k_geom<true><<<nblk(g.pstride, 128), 128, 0, s>>>(geo, g, m, ctl, half, t_fixed);
+    else k_geom<false><<<nblk(g.pstride, 128), 128, 0, s>>>(geo, g, m, ctl, half, t_fixed);
 }
 
 void launch_vol_from_geo(const double *geo, double *vol, const Geo &g, cudaStream_t s)
@@ -193,9 +224,11 @@ void launch_residual_mapped(const double *Fx, const double *Fy, const double *Fz
     k_residual_mapped<<<nblk(g.ncell, 256), 256, 0, s>>>(Fx, Fy, Fz, geo, g, L, dL);
 }
 
-void launch_cfl_mapped(const double *Q, const double *geo, const Geo &g, double gamma, Ctl *ctl, cudaStream_t s)
+void launch_cfl_mapped(const double *Q, const double *geo, const Geo &g, double gamma, Ctl *ctl, cudaStream_t s,
+                       bool mixed)
 {
-    k_cfl_mapped<<<nblk(g.ncell, 256), 256, 0, s>>>(Q, geo, g, gamma, ctl);
+    if (mixed) k_cfl_mapped<true><<<nblk(g.ncell, 256), 256, 0, s>>>(Q, geo, g, gamma, ctl);
+    else k_cfl_mapped<false><<<nblk(g.ncell, 256), 256, 0, s>>>(Q, geo, g, gamma, ctl);
 }
 
 template void launch_recon_mapped<double>(const double *, const double *, double *, unsigned char *, const Geo &,

@@ -20,7 +20,7 @@ struct MapGeo {
     const double *sx, *sy, *sz;
     // FP32 copies for the mixed path's face geometry: lo, the reference
     // spacing (hi - lo)/n, and the sine factors
-    float lof[3], hf[3];
+    float lof[3], hf[3], ihf[3];
     const float *sxf, *syf, *szf;
     // mixed path (null otherwise): an FP32 copy of the cells' central second
     // moments, [6][pstride], written by the geometry kernel, and the split
@@ -137,6 +137,84 @@ HK_HD void cell_geometry(const MapGeo &m, int i, int j, int k, double S, double 
     out[0] = vol;
     for (int d = 0; d < 3; ++d) out[1 + d] = xc[d] + cy[d];
     for (int e = 0; e < 6; ++e) out[4 + e] = M[e] * ivol;
+}
+
+// The same record for the mixed path, with the small quantities in FP32:
+// the relative Jacobian 1 + sum_e (dD/dp_e)/h_e, the point offsets
+// p h + D about the reference centre, the centroid offset and the central
+// moments are all of the size of a cell (or of the displacement), so FP32
+// keeps them to about 1e-7 relative, the precision of the reconstruction
+// that reads them; the volume h_x h_y h_z (relative volume) and the centroid
+// xi_c + offset are assembled in FP64.  fm receives the central moments in
+// FP32 (the copy the FP32 reconstruction reads).
+__device__ __forceinline__ void cell_geometry_mixed(const MapGeo &m, int i, int j, int k, float aS,
+                                                    double out[NGEO], float fm[6])
+{
+    const float g = float(GAUSS_S);
+    float sv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        sv[q] = m.sxf[i + (q & 1) + GHOST] * m.syf[j + ((q >> 1) & 1) + GHOST] * m.szf[k + (q >> 2) + GHOST];
+    const float wv[2][2] = {{0.5f + g, 0.5f - g}, {0.5f - g, 0.5f + g}};
+    float ax[2][4], dax[4];
+#pragma unroll
+    for (int yz = 0; yz < 4; ++yz) {
+        const float v0 = sv[2 * yz], v1 = sv[2 * yz + 1];
+        dax[yz] = v1 - v0;
+#pragma unroll
+        for (int ix = 0; ix < 2; ++ix) ax[ix][yz] = v0 * wv[ix][0] + v1 * wv[ix][1];
+    }
+    float axy[2][2][2], dxy[2][2], dyx[2][2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+#pragma unroll
+        for (int iy = 0; iy < 2; ++iy) {
+#pragma unroll
+            for (int ix = 0; ix < 2; ++ix)
+                axy[ix][iy][c] = ax[ix][2 * c] * wv[iy][0] + ax[ix][2 * c + 1] * wv[iy][1];
+            dxy[iy][c] = dax[2 * c] * wv[iy][0] + dax[2 * c + 1] * wv[iy][1];
+        }
+#pragma unroll
+        for (int ix = 0; ix < 2; ++ix) dyx[ix][c] = ax[ix][2 * c + 1] - ax[ix][2 * c];
+    }
+    float Y[8][3], w[8], vr = 0.0f, m1[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int ix = q & 1, iy = (q >> 1) & 1, iz = q >> 2;
+        const float p[3] = {ix ? g : -g, iy ? g : -g, iz ? g : -g};
+        const float D = aS * (axy[ix][iy][0] * wv[iz][0] + axy[ix][iy][1] * wv[iz][1]);
+        const float gD[3] = {dxy[iy][0] * wv[iz][0] + dxy[iy][1] * wv[iz][1],
+                             dyx[ix][0] * wv[iz][0] + dyx[ix][1] * wv[iz][1], axy[ix][iy][1] - axy[ix][iy][0]};
+        // relative Jacobian times the Gauss weight 1/8
+        w[q] = 0.125f * fabsf(1.0f + aS * (gD[0] * m.ihf[0] + gD[1] * m.ihf[1] + gD[2] * m.ihf[2]));
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Y[q][d] = p[d] * m.hf[d] + D;
+        vr += w[q];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) m1[d] += w[q] * Y[q][d];
+    }
+    const float ivr = 1.0f / vr;
+    const float cy[3] = {m1[0] * ivr, m1[1] * ivr, m1[2] * ivr};
+    float M[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const float dx = Y[r][0] - cy[0], dy = Y[r][1] - cy[1], dz = Y[r][2] - cy[2];
+        M[0] += w[r] * dx * dx;
+        M[1] += w[r] * dy * dy;
+        M[2] += w[r] * dz * dz;
+        M[3] += w[r] * dx * dy;
+        M[4] += w[r] * dx * dz;
+        M[5] += w[r] * dy * dz;
+    }
+    const int idx[3] = {i, j, k};
+    out[0] = m.h[0] * m.h[1] * m.h[2] * double(vr);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) out[1 + d] = (m.lo[d] + ((double)idx[d] + 0.5) * m.h[d]) + double(cy[d]);
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+        fm[e] = M[e] * ivr;
+        out[4 + e] = double(fm[e]);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -20,6 +20,7 @@ void launch_update_mapped(int stage, double *Qn, double *Qs, double *Wacc, doubl
                           cudaStream_t s);
 void launch_residual_mapped(const double *Fx, const double *Fy, const double *Fz, const double *geo, const Geo &g,
                             double *L, double *dL, cudaStream_t s);
-void launch_cfl_mapped(const double *Q, const double *geo, const Geo &g, double gamma, Ctl *ctl, cudaStream_t s);
+void launch_cfl_mapped(const double *Q, const double *geo, const Geo &g, double gamma, Ctl *ctl, cudaStream_t s,
+                       bool mixed = false);
 
 }  // namespace hk
