@@ -276,7 +276,7 @@ void hgks_batch_destroy(hgks_batch_t *b);
  * Working memory is one file-scope device array of HGKS_NOALLOC_SCRATCH_BYTES
  * that every GPU loading the library holds until the process exits.  The
  * grid's padded state, reconstruction coefficients and face fluxes must fit
- * in it: cubes of up to 28^3 cells in FP64 and 31^3 mixed; larger
+ * in it (mixed: also the split state): cubes of up to 27^3 cells in FP64 and 29^3 mixed; larger
  * grids return HGKS_E_INVALID with the byte count in hgks_last_error(NULL).
  * The first call on a device looks up the array's device address with that
  * device current (cudaGetSymbolAddress); make that first call before any

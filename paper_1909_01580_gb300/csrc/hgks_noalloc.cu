@@ -135,7 +135,8 @@ extern "C" int hgks_flux_noalloc(const hgks_grid_t *grid, double gamma, double m
     hk::scheme_derive(S);
 
     // carve the scratch: control block, padded state, coefficients, flags,
-    // face fluxes of the three axes
+    // face fluxes of the three axes, and (mixed) the split state Q_hi + Q_lo
+    // that the handle's mixed path reconstructs from
     const bool mixed = grid->precision == HGKS_MIXED;
     const size_t rsz = mixed ? sizeof(float) : sizeof(double);
     size_t off_ctl = 0;
@@ -149,6 +150,8 @@ extern "C" int hgks_flux_noalloc(const hgks_grid_t *grid, double gamma, double m
         off_f[d] = end;
         end += round256(10 * nf * sizeof(double));
     }
+    const size_t off_split = end;
+    if (mixed) end += round256(2 * 5 * (size_t)g.pstride * sizeof(float));
     if (end > (size_t)HGKS_NOALLOC_SCRATCH_BYTES) {
         char msg[256];
         snprintf(msg, sizeof msg,
@@ -167,19 +170,21 @@ extern "C" int hgks_flux_noalloc(const hgks_grid_t *grid, double gamma, double m
     void *coef = sb + off_coef;
     unsigned char *flag = sb + off_flag;
     double *F[3] = {(double *)(sb + off_f[0]), (double *)(sb + off_f[1]), (double *)(sb + off_f[2])};
+    float *split = mixed ? (float *)(sb + off_split) : nullptr;
     cudaStream_t s = (cudaStream_t)stream;
 
     // Every byte a kernel reads below is written earlier in this call: the
     // control block (time, dt, counters) by k_set_ctl, the interior state by
     // the scatter, every ghost cell by the halo, every coefficient and flag
     // of the reconstruction box by the reconstruction, every face flux by
-    // the flux kernels.  Nothing of an earlier call is read.
+    // the flux kernels, and (mixed) the split state by the split kernel before
+    // the reconstruction reads it.  Nothing of an earlier call is read.
     hk::launch_init_ctl(ctl, 0.0, s);
     hk::launch_set_ctl(ctl, 0.0, dt, 1, s);
     hk::launch_scatter(q, Q, g, s);
     hk::launch_halo(Q, g, s);
     if (mixed) {
-        hk::launch_recon<float>(Q, (float *)coef, flag, g, S, ctl, s);
+        hk::launch_recon<float>(Q, (float *)coef, flag, g, S, ctl, s, split);
         for (int d = 0; d < 3; ++d) hk::launch_flux<float>(d, (const float *)coef, F[d], g, S, ctl, s);
     } else {
         hk::launch_recon<double>(Q, (double *)coef, flag, g, S, ctl, s);
