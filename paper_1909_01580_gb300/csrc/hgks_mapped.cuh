@@ -49,14 +49,6 @@ HK_HD void vertex_pos(const MapGeo &m, int i, int j, int k, double S, double x[3
     for (int d = 0; d < 3; ++d) x[d] = (m.lo[d] + (m.hi[d] - m.lo[d]) * (double)idx[d] / (double)m.n[d]) + disp;
 }
 
-// vertex velocity: amp omega cos(omega t) times the sine factor (moving mesh)
-HK_HD void vertex_vel(const MapGeo &m, int i, int j, int k, double C, double v[3])
-{
-    const double s = m.sx[i + GHOST] * m.sy[j + GHOST] * m.sz[k + GHOST];
-    const double vel = m.moving ? m.amp * m.omega * C * s : 0.0;
-    v[0] = v[1] = v[2] = vel;
-}
-
 // volume, centroid and central second moments of cell (i,j,k) by the 2x2x2
 // Gauss rule on its trilinear map (weights 1/8 times |det J|).  The map
 // adds the same scalar D(p) = amp S sum_v psi_v(p) s_v to every coordinate
@@ -564,12 +556,6 @@ __device__ __forceinline__ void big_offset_rt(int s, int o[3])
     o[2] = p / 9 - 1;
 }
 
-// index s of the big-stencil neighbour at offset o (inverse of big_offset_rt)
-__device__ __forceinline__ int big_index(const int o[3])
-{
-    const int p = (o[2] + 1) * 9 + (o[1] + 1) * 3 + (o[0] + 1);
-    return p - (p > 0) - (p > 2) - (p > 6) - (p > 8) - (p > 13) - (p > 18) - (p > 20) - (p > 24);
-}
 
 // row of the big-stencil system for neighbour s from the staged offsets and
 // the neighbour's second moments
@@ -612,36 +598,6 @@ __device__ __forceinline__ R staged_dq(const R *sh, const double *__restrict__ Q
     else return R(Q[v * g.pstride + pn] - qc);
 }
 
-// the 8 vertices of cell (i,j,k), vertex (a,b,c) at V[a + 2b + 4c]
-__device__ __forceinline__ void cell_vertices(const MapGeo &m, int i, int j, int k, double S, double V[8][3])
-{
-#pragma unroll
-    for (int q = 0; q < 8; ++q) vertex_pos(m, i + (q & 1), j + ((q >> 1) & 1), k + (q >> 2), S, V[q]);
-}
-
-// face Gauss point gq of the cell with vertices V, in its scaled frame
-// (same points and order as cell_gauss_point)
-__device__ __forceinline__ void gauss_from_vertices(const double V[8][3], int gq, const double c[3], double h,
-                                                    double X[3])
-{
-    const int d = gq / 8, side = (gq / 4) & 1, ga = (gq >> 1) & 1, gb = gq & 1;
-    double p[3];
-    p[d] = side ? 0.5 : -0.5;
-    p[(d + 1) % 3] = ga ? GAUSS_S : -GAUSS_S;
-    p[(d + 2) % 3] = gb ? GAUSS_S : -GAUSS_S;
-    double x[3] = {0, 0, 0};
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int a = q & 1, b = (q >> 1) & 1, cc = q >> 2;
-        const double psi = 0.125 * (1.0 + 2.0 * (2 * a - 1) * p[0]) * (1.0 + 2.0 * (2 * b - 1) * p[1]) *
-                           (1.0 + 2.0 * (2 * cc - 1) * p[2]);
-#pragma unroll
-        for (int e = 0; e < 3; ++e) x[e] += V[q][e] * psi;
-    }
-#pragma unroll
-    for (int e = 0; e < 3; ++e) X[e] = (x[e] - c[e]) / h;
-}
-
 // least-squares operator of sub-stencil M on a trilinear cell: b = P dq for
 // the data dq of its 4 cells, P = (R^T R)^{-1} R^T with R the 4 x 3 linear
 // rows; formed once per cell and applied to the five variables
@@ -666,7 +622,7 @@ __device__ __forceinline__ void sub_offsets_rt(int M, int o[4][3])
 
 // big-stencil indices (0..17) of the 4 cells of each sub-stencil, 5 bits
 // each, built at compile time from the same enumerations as
-// sub_offsets_rt and big_index; read from constant memory by the run-time
+// sub_offsets_rt and the big-stencil enumeration; read from constant memory by the run-time
 // sub-stencil loop (the index is uniform over the warp)
 struct SubIdxTable {
     unsigned w[24];
