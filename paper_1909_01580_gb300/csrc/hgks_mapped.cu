@@ -57,8 +57,14 @@ __global__ void k_vol_from_geo(const double *__restrict__ geo, double *__restric
     vol[t] = geo[pidx(g, i, j, k)];
 }
 
+// resident blocks per SM asked of the compiler for the mapped
+// reconstruction: the FP32 kernel fits 6 (its shared-memory limit) in 168
+// registers without spilling (221 otherwise, 4 blocks)
+template <typename R> struct MapReconOcc { static constexpr int blocks = 1; };
+template <> struct MapReconOcc<float> { static constexpr int blocks = 6; };
+
 template <typename R>
-__global__ void __launch_bounds__(RM_BS) k_recon_mapped(const double *__restrict__ Q, const double *__restrict__ geo,
+__global__ void __launch_bounds__(RM_BS, MapReconOcc<R>::blocks) k_recon_mapped(const double *__restrict__ Q, const double *__restrict__ geo,
                                                         R *__restrict__ coef, unsigned char *__restrict__ flag, Geo g,
                                                         MapGeo m, Scheme S, Ctl *ctl, int half)
 {
@@ -85,8 +91,14 @@ __global__ void __launch_bounds__(128) k_positivity_mapped(const double *__restr
                               (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
+// resident blocks of 128 threads per SM asked of the compiler for the mapped
+// face flux: the FP32 kernel fits 4 in 128 registers without spilling
+// (about 200 registers otherwise)
+template <typename R> struct MapFluxOcc { static constexpr int blocks = 1; };
+template <> struct MapFluxOcc<float> { static constexpr int blocks = 4; };
+
 template <typename R, int D>
-__global__ void __launch_bounds__(128) k_flux_mapped(const R *__restrict__ coef, double *__restrict__ Fout, Geo g,
+__global__ void __launch_bounds__(128, MapFluxOcc<R>::blocks) k_flux_mapped(const R *__restrict__ coef, double *__restrict__ Fout, Geo g,
                                                      MapGeo m, Scheme S, Ctl *ctl, int half)
 {
     if (!ctl->active) return;
