@@ -649,6 +649,23 @@ constexpr SubIdxTable make_sub_idx()
     }
     return t;
 }
+// every sub-stencil names 4 distinct neighbours of the 18, and the 24
+// sub-stencils are distinct
+constexpr bool sub_idx_valid(const SubIdxTable &t)
+{
+    for (int M = 0; M < 24; ++M) {
+        for (int q = 0; q < 4; ++q) {
+            const unsigned a = (t.w[M] >> (5 * q)) & 31u;
+            if (a >= 18u) return false;
+            for (int r = 0; r < q; ++r)
+                if (((t.w[M] >> (5 * r)) & 31u) == a) return false;
+        }
+        for (int N = 0; N < M; ++N)
+            if (t.w[N] == t.w[M]) return false;
+    }
+    return (t.w[0] >> 20) == 0u;
+}
+static_assert(sub_idx_valid(make_sub_idx()), "sub-stencil index table");
 static __constant__ SubIdxTable kSubIdx = make_sub_idx();
 __device__ __forceinline__ int sub_cell(unsigned w, int q) { return (int)((w >> (5 * q)) & 31u); }
 
