@@ -37,8 +37,8 @@ UNIT = "cell-stage updates/s"
 # Work per unit of the dominant kernel (the Gauss-point face flux): FP64
 # flop per Gauss point executed on the FP64 pipe (2 per DFMA, 1 per DADD and
 # DMUL) for the FP64 path, FP32 flop on the FMA pipe for the mixed path,
-# from the ncu instruction counters of one capture of the kernel on TGV 32^3
-# (profiles/k_face_flux_tgv32.md).  Per-launch DRAM traffic of the same
+# from the ncu instruction counters of one capture of the kernel on TGV
+# 32^3.  Per-launch DRAM traffic of the same
 # capture, scaled by the faces of a 128^3 launch (traffic grows with the
 # cells: the coefficient array is read once).
 FLUX_FP64_FLOP_PER_GP = 3042.0
@@ -57,6 +57,23 @@ def _dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(x, dist=None, device="cuda"):
+    """The largest x over the ranks (the timed region of the slowest rank);
+    x itself on one process."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_rate(world, units_per_rank, seconds):
+    """Whole-job throughput of `world` independent replicas (weak scaling):
+    the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
 
 
 class ClockSampler:
@@ -142,12 +159,7 @@ def run_gpu(args, rank, world, local, dist):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    slowest = functools.partial(max_over_ranks, dist=dist, device="cuda")
 
     results = {}
     for prec_name, prec in (("fp64", hgks.HGKS_FP64), ("mixed", hgks.HGKS_MIXED)):
@@ -172,7 +184,7 @@ def run_gpu(args, rank, world, local, dist):
         clocks = sampler.stop()
         launches = s.launches - l0
         ms = ev0.elapsed_time(ev1)
-        ms_max = max_over_ranks(ms)
+        ms_max = slowest(ms)
         timing = hgks.hgks_get_timing(s.h)
         hgks.hgks_set_timing(s.h, 0)
         t_now, steps_done = s.step(0)
@@ -186,7 +198,7 @@ def run_gpu(args, rank, world, local, dist):
         peak = PEAK_FP64_TFLOPS if prec_name == "fp64" else PEAK_FP32_TFLOPS
         total_phase = sum(v[0] for v in timing.values())
         results[prec_name] = {
-            "value": world * ncell * 2 * args.steps / (ms_max / 1e3),
+            "value": replicas_rate(world, ncell * 2 * args.steps, ms_max / 1e3),
             "ms_per_step": ms_max / args.steps,
             "launches": launches,
             "clocks": clocks,
@@ -215,8 +227,8 @@ def run_gpu(args, rank, world, local, dist):
                 s.step(1, cfl=0.35)
                 hgks.hgks_get_state(s.h, out_np)
             barrier()
-            el = max_over_ranks(time.perf_counter() - t0)
-            results[prec_name]["e2e"] = {"value": world * ncell * 2 * e2e_steps / el, "unit": UNIT,
+            el = slowest(time.perf_counter() - t0)
+            results[prec_name]["e2e"] = {"value": replicas_rate(world, ncell * 2 * e2e_steps, el), "unit": UNIT,
                                          "h2d_bytes_per_step": int(q0.nbytes), "d2h_bytes_per_step": int(q0.nbytes),
                                          "steps": e2e_steps}
         s.close()
