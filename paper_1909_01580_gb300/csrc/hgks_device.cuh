@@ -219,7 +219,13 @@ template <typename R> HK_HD void bmom_tangential(BMom<R> &B, R th, R K)
 // x = T x' (in place)
 template <typename R> HK_HD void boost_out(R V, R W, R x[5])
 {
-    x[4] += V * x[2] + W * x[3] + R(0.5) * (V * V + W * W) * x[0];
+    // x4 + V x2 + W x3 + (V^2 + W^2)/2 x0 as a chain of multiply-adds
+    const R k = R(0.5) * (V * V + W * W);
+    R e = x[4];
+    e += V * x[2];
+    e += W * x[3];
+    e += k * x[0];
+    x[4] = e;
     x[2] += V * x[0];
     x[3] += W * x[0];
 }
@@ -229,8 +235,24 @@ template <typename R> HK_HD void boost_in(R V, R W, R b[5])
 {
     b[2] -= V * b[0];
     b[3] -= W * b[0];
-    b[4] -= V * b[2] + W * b[3] + R(0.5) * (V * V + W * W) * b[0];
+    // b4 - V b2' - W b3' - (V^2 + W^2)/2 b0 as a chain of multiply-adds
+    R e = b[4];
+    e -= V * b[2];
+    e -= W * b[3];
+    e -= (R(0.5) * (V * V + W * W)) * b[0];
+    b[4] = e;
 }
+
+// The moment combinations below depend only on the Maxwellian and on n, so
+// the compiler shares them between the calls for one Maxwellian; what is
+// left per call is a few multiply-adds with the slope c.
+//   E0 = <u^n E'>, E1 = <u^{n+1} E'>, E2 = <u^n E'^2>, Q = <u^n v'^2 E'>.
+template <int N, typename R> HK_HD R bm_E0(const BMom<R> &B) { return R(0.5) * (B.m[N + 2] + B.r1 * B.m[N]); }
+template <int N, typename R> HK_HD R bm_E2(const BMom<R> &B)
+{
+    return R(0.25) * (B.m[N + 4] + R(2) * B.r1 * B.m[N + 2] + B.r2 * B.m[N]);
+}
+template <int N, typename R> HK_HD R bm_Q(const BMom<R> &B) { return R(0.5) * (B.th * B.m[N + 2] + B.vr * B.m[N]); }
 
 // <u^n psi'>
 template <int N, typename R> HK_HD void bpsi(const BMom<R> &B, R o[5])
@@ -238,22 +260,29 @@ template <int N, typename R> HK_HD void bpsi(const BMom<R> &B, R o[5])
     o[0] = B.m[N];
     o[1] = B.m[N + 1];
     o[2] = o[3] = R(0);
-    o[4] = R(0.5) * (B.m[N + 2] + B.r1 * B.m[N]);
+    o[4] = bm_E0<N>(B);
 }
 
 // <u^n (c . psi') psi'>
 template <int N, typename R> HK_HD void bapsi(const BMom<R> &B, const R c[5], R o[5])
 {
     const R *m = B.m;
-    const R e0 = m[N + 2] + B.r1 * m[N];          // 2 <u^n E'>
-    const R e1 = m[N + 3] + B.r1 * m[N + 1];      // 2 <u^{n+1} E'>
-    const R e2 = m[N + 4] + R(2) * B.r1 * m[N + 2] + B.r2 * m[N];  // 4 <u^n E'^2>
-    const R h4 = R(0.5) * c[4];
-    o[0] = c[0] * m[N] + c[1] * m[N + 1] + h4 * e0;
-    o[1] = c[0] * m[N + 1] + c[1] * m[N + 2] + h4 * e1;
-    o[2] = c[2] * B.th * m[N];
-    o[3] = c[3] * B.th * m[N];
-    o[4] = R(0.5) * (c[0] * e0 + c[1] * e1 + h4 * e2);
+    const R E0 = bm_E0<N>(B), E1 = bm_E0<N + 1>(B), E2 = bm_E2<N>(B);
+    const R tm = B.th * m[N];
+    R e = c[0] * m[N];
+    e += c[1] * m[N + 1];
+    e += c[4] * E0;
+    o[0] = e;
+    e = c[0] * m[N + 1];
+    e += c[1] * m[N + 2];
+    e += c[4] * E1;
+    o[1] = e;
+    o[2] = c[2] * tm;
+    o[3] = c[3] * tm;
+    e = c[0] * E0;
+    e += c[1] * E1;
+    e += c[4] * E2;
+    o[4] = e;
 }
 
 // <u^n v' (c . psi') psi'> (T = 0) or <u^n w' (c . psi') psi'> (T = 1)
@@ -261,13 +290,15 @@ template <int N, int T, typename R> HK_HD void bapsi_t(const BMom<R> &B, const R
 {
     const R *m = B.m;
     const R ct = T ? c[3] : c[2];
-    const R q = B.th * m[N + 2] + B.vr * m[N];  // 2 <u^n v'^2 E'>
-    o[0] = ct * B.th * m[N];
-    o[1] = ct * B.th * m[N + 1];
-    const R diag = B.th * (c[0] * m[N] + c[1] * m[N + 1]) + R(0.5) * c[4] * q;
+    const R tm0 = B.th * m[N], tm1 = B.th * m[N + 1], Q = bm_Q<N>(B);
+    o[0] = ct * tm0;
+    o[1] = ct * tm1;
+    R diag = c[0] * tm0;
+    diag += c[1] * tm1;
+    diag += c[4] * Q;
     o[2] = T ? R(0) : diag;
     o[3] = T ? diag : R(0);
-    o[4] = R(0.5) * ct * q;
+    o[4] = ct * Q;
 }
 
 template <typename R> struct Prim {
@@ -302,11 +333,19 @@ template <typename R> HK_HD Prim<R> primitive(const R Wc[5], R gamma, R Kp3, R i
 template <typename R> HK_HD void micro_slope_u(const Prim<R> &s, const R b[5], R a[5])
 {
     const R r1 = b[1] - s.U * b[0];
-    a[4] = s.c4 * (R(2) * b[4] - s.q2 * b[0] - R(2) * s.U * r1);
-    a[1] = R(2) * s.lam * r1 - s.U * a[4];
-    a[2] = R(2) * s.lam * b[2];
-    a[3] = R(2) * s.lam * b[3];
-    a[0] = b[0] - s.U * a[1] - R(0.5) * a[4] * s.q2;
+    // a4 = c4 (2 b4 - q2 b0 - 2 U r1); the products of the Maxwellian's
+    // constants are shared between the calls for one Maxwellian
+    R e = (R(2) * s.c4) * b[4];
+    e -= (s.c4 * s.q2) * b[0];
+    e -= (R(2) * s.c4 * s.U) * r1;
+    a[4] = e;
+    const R l2 = R(2) * s.lam;
+    a[1] = l2 * r1 - s.U * a[4];
+    a[2] = l2 * b[2];
+    a[3] = l2 * b[3];
+    e = b[0] - s.U * a[1];
+    e -= (R(0.5) * s.q2) * a[4];
+    a[0] = e;
 }
 
 // out += dF_i, the derivative of the Euler flux in direction i for the
@@ -320,12 +359,26 @@ HK_HD void euler_dflux(const Prim<R> &s, const R Wc[5], R ir, R gm1, const R d[5
     R du[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) du[j] = (d[1 + j] - u[j] * d[0]) * ir;
-    const R dp = gm1 * (d[4] - (s.U * d[1] + s.V * d[2] + s.W * d[3]) + R(0.5) * (s.U * s.U + s.V * s.V + s.W * s.W) * d[0]);
+    // dp = (gamma - 1)(d4 + |u|^2/2 d0 - u . d), as a chain of multiply-adds
+    R e = d[4];
+    e += (R(0.5) * (s.U * s.U + s.V * s.V + s.W * s.W)) * d[0];
+    e -= s.U * d[1];
+    e -= s.V * d[2];
+    e -= s.W * d[3];
+    const R dp = gm1 * e;
     out[0] += d[1 + I];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) out[1 + j] += d[1 + I] * u[j] + Wc[1 + I] * du[j];
+    for (int j = 0; j < 3; ++j) {
+        R o = out[1 + j];
+        o += d[1 + I] * u[j];
+        o += Wc[1 + I] * du[j];
+        out[1 + j] = o;
+    }
     out[1 + I] += dp;
-    out[4] += du[I] * (Wc[4] + s.p) + u[I] * (d[4] + dp);
+    R o4 = out[4];
+    o4 += du[I] * (Wc[4] + s.p);
+    o4 += u[I] * (d[4] + dp);
+    out[4] = o4;
 }
 
 // ---------------------------------------------------------------------------
@@ -530,10 +583,24 @@ HK_HD void gks_flux(const R Wl[5], const R dWl[3][5], const R Wr[5], const R dWr
     R d0 = R(4) * r * Dq * idt, d3 = -d0, d2 = R(1) - tau * d0, d5 = tau * d0;
     R d1 = R(4) * r * (e2 - e1) - R(8) * r * r * Dq, d4 = -d1;
 
+    const R rc0 = s0.rho * c0, rc1 = s0.rho * c1, rc2 = s0.rho * c2;
+    const R rd0 = s0.rho * d0, rd1 = s0.rho * d1, rd2 = s0.rho * d2;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-        F[k] = s0.rho * (c0 * F0a[k] + c1 * F0b[k] + c2 * F0c[k]) + c3 * Fa[k] + c4 * Fb[k] + c5 * Fc[k];
-        dF[k] = s0.rho * (d0 * F0a[k] + d1 * F0b[k] + d2 * F0c[k]) + d3 * Fa[k] + d4 * Fb[k] + d5 * Fc[k];
+        R e = rc0 * F0a[k];
+        e += rc1 * F0b[k];
+        e += rc2 * F0c[k];
+        e += c3 * Fa[k];
+        e += c4 * Fb[k];
+        e += c5 * Fc[k];
+        F[k] = e;
+        e = rd0 * F0a[k];
+        e += rd1 * F0b[k];
+        e += rd2 * F0c[k];
+        e += d3 * Fa[k];
+        e += d4 * Fb[k];
+        e += d5 * Fc[k];
+        dF[k] = e;
     }
     if (prfix) {
         // heat flux about U0 of the time-integrated distribution:
