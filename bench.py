@@ -41,9 +41,9 @@ UNIT = "cell-stage updates/s"
 # 32^3.  Per-launch DRAM traffic of the same
 # capture, scaled by the faces of a 128^3 launch (traffic grows with the
 # cells: the coefficient array is read once).
-FLUX_FP64_FLOP_PER_GP = 3042.0
-FLUX_FP32_FLOP_PER_GP = 2803.0
-FLUX_TRAFFIC_BYTES_PER_FACE = {"fp64": 14.306e6 / 33792, "mixed": 7.212e6 / 33792}
+FLUX_FP64_FLOP_PER_GP = 3018.0
+FLUX_FP32_FLOP_PER_GP = 2769.0
+FLUX_TRAFFIC_BYTES_PER_FACE = {"fp64": 14.300e6 / 33792, "mixed": 7.209e6 / 33792}
 # GB300 ALU peaks derived from unit counts and clocks: 152 SMs x 2070 MHz x
 # (FP64: 2 DFMA/clk/SM = 4 flop; FP32: 128 FMA/clk/SM = 256 flop).
 SM_COUNT = 152
