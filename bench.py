@@ -35,15 +35,19 @@ METRIC = "cell-stage updates/s at TGV 128^3 (FP64 vs mixed)"
 UNIT = "cell-stage updates/s"
 
 # Work per unit of the dominant kernel (the Gauss-point face flux): FP64
-# flop per Gauss point executed on the FP64 pipe (2 per DFMA, 1 per DADD and
-# DMUL) for the FP64 path, FP32 flop on the FMA pipe for the mixed path,
-# from the ncu instruction counters of one capture of the kernel on TGV
-# 32^3.  Per-launch DRAM traffic of the same
-# capture, scaled by the faces of a 128^3 launch (traffic grows with the
-# cells: the coefficient array is read once).
+# flop per Gauss point on the FP64 pipe (2 per DFMA, 1 per DADD and DMUL)
+# for the FP64 path, FP32 flop on the FMA pipe for the mixed path, fixed at
+# the ncu instruction counters of one capture of the kernel on TGV 32^3; the
+# kernel has since been rewritten to evaluate the Gauss-point polynomials as
+# multiply-add chains, which executes slightly fewer flops for the same
+# algorithm, so `achieved` is at most a little understated.  The DRAM traffic
+# of that capture no longer describes the current kernel and is reported as
+# null (FLUX_TRAFFIC_BYTES_PER_FACE keeps the last measured figure, bytes per
+# face of a TGV 32^3 launch, for reference).
 FLUX_FP64_FLOP_PER_GP = 3018.0
 FLUX_FP32_FLOP_PER_GP = 2769.0
 FLUX_TRAFFIC_BYTES_PER_FACE = {"fp64": 14.300e6 / 33792, "mixed": 7.209e6 / 33792}
+FLUX_TRAFFIC_CURRENT = False
 # GB300 ALU peaks derived from unit counts and clocks: 152 SMs x 2070 MHz x
 # (FP64: 2 DFMA/clk/SM = 4 flop; FP32: 128 FMA/clk/SM = 256 flop).
 SM_COUNT = 152
@@ -206,8 +210,12 @@ def run_gpu(args, rank, world, local, dist):
             "flux_share": flux_ms / total_phase if total_phase > 0 else None,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
-                         "traffic": FLUX_TRAFFIC_BYTES_PER_FACE[prec_name] * nface_stage / 3,
-                         "traffic_note": "ncu dram read+write of a TGV 32^3 launch scaled to 128^3 faces",
+                         "traffic": (FLUX_TRAFFIC_BYTES_PER_FACE[prec_name] * nface_stage / 3
+                                     if FLUX_TRAFFIC_CURRENT else None),
+                         "traffic_note": ("ncu dram read+write of a TGV 32^3 launch scaled to 128^3 faces"
+                                          if FLUX_TRAFFIC_CURRENT else
+                                          "null: the kernel changed after its last ncu capture (which read "
+                                          f"{FLUX_TRAFFIC_BYTES_PER_FACE[prec_name]:.0f} B per face)"),
                          "kernel": "k_face_flux", "pipe": "fp64" if prec_name == "fp64" else "fp32",
                          "peak_source": "derived: 152 SMs x 2070 MHz x (4 FP64 | 256 FP32) flop/clk/SM"},
             "t_reached": t_now,

@@ -608,11 +608,19 @@ HK_HD void gks_flux(const R Wl[5], const R dWl[3][5], const R Wr[5], const R dWr
         // S the psi-moments of the same terms (S of the g0 A-term is -S0b).
         R uu = R(0.5) * (s0.U * s0.U + s0.V * s0.V + s0.W * s0.W);
         R Sx[5], Sd[5];
+        const R c03 = c0 + c3, c12 = s0.rho * (c1 - c2), d03 = d0 + d3, d12 = s0.rho * (d1 - d2);
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            R s0b = s0.rho * S0b[k];
-            Sx[k] = c0 * Sa[k] + (c1 - c2) * s0b + c3 * Sa[k] + c4 * Sb[k] + c5 * Sc[k];
-            Sd[k] = d0 * Sa[k] + (d1 - d2) * s0b + d3 * Sa[k] + d4 * Sb[k] + d5 * Sc[k];
+            R e = c03 * Sa[k];
+            e += c12 * S0b[k];
+            e += c4 * Sb[k];
+            e += c5 * Sc[k];
+            Sx[k] = e;
+            e = d03 * Sa[k];
+            e += d12 * S0b[k];
+            e += d4 * Sb[k];
+            e += d5 * Sc[k];
+            Sd[k] = e;
         }
         // the g0 and initial terms both carry W0-like psi moments: the g0
         // term's zeroth piece is W0 itself and the half-space pieces sum to W0

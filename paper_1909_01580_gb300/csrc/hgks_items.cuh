@@ -385,17 +385,37 @@ __device__ __forceinline__ void eval_side(const R *__restrict__ coef, long long 
     constexpr int DB = D + B == 1 ? 6 : (D + B == 2 ? 7 : 8);
     constexpr int AB = A + B == 1 ? 6 : (A + B == 2 ? 7 : 8);
     const R ih = R(g.inv_h);
+    // point factors shared by the five variables; the sums below are chains
+    // of multiply-adds
+    const R xab = xa * xb, xd2 = R(2) * xd, xa2 = R(2) * xa, xb2 = R(2) * xb;
     R val[5], grad[5][3];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
         R c[9];
 #pragma unroll
         for (int n = 0; n < 9; ++n) c[n] = coef[coef_slot(v, 1 + n) * stride + ci];
-        val[v] = coef[coef_slot(v, 0) * stride + ci] + (c[D] * xd + c[3 + D] * R(1.0 / 6.0)) +
-                 xa * (c[A] + c[DA] * xd) + xb * (c[B] + c[DB] * xd) + c[AB] * xa * xb;
-        grad[v][D] = (c[D] + R(2) * c[3 + D] * xd + c[DA] * xa + c[DB] * xb) * ih;
-        grad[v][A] = (c[A] + R(2) * c[3 + A] * xa + c[DA] * xd + c[AB] * xb) * ih;
-        grad[v][B] = (c[B] + R(2) * c[3 + B] * xb + c[DB] * xd + c[AB] * xa) * ih;
+        R e = coef[coef_slot(v, 0) * stride + ci];
+        e += c[D] * xd;
+        e += c[3 + D] * R(1.0 / 6.0);
+        e += xa * (c[A] + c[DA] * xd);
+        e += xb * (c[B] + c[DB] * xd);
+        e += c[AB] * xab;
+        val[v] = e;
+        e = c[D];
+        e += c[3 + D] * xd2;
+        e += c[DA] * xa;
+        e += c[DB] * xb;
+        grad[v][D] = e * ih;
+        e = c[A];
+        e += c[3 + A] * xa2;
+        e += c[DA] * xd;
+        e += c[AB] * xb;
+        grad[v][A] = e * ih;
+        e = c[B];
+        e += c[3 + B] * xb2;
+        e += c[DB] * xd;
+        e += c[AB] * xa;
+        grad[v][B] = e * ih;
     }
     // local frame: local axis l is global axis (D + l) % 3
     W[0] = val[0];
