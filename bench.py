@@ -37,13 +37,15 @@ UNIT = "cell-stage updates/s"
 # Work per unit of the dominant kernel (the Gauss-point face flux): FP64
 # flop per Gauss point on the FP64 pipe (2 per DFMA, 1 per DADD and DMUL)
 # for the FP64 path, FP32 flop on the FMA pipe for the mixed path, fixed at
-# the ncu instruction counters of one capture of the kernel on TGV 32^3; the
-# kernel has since been rewritten to evaluate the Gauss-point polynomials as
-# multiply-add chains, which executes slightly fewer flops for the same
-# algorithm, so `achieved` is at most a little understated.  The DRAM traffic
-# of that capture no longer describes the current kernel and is reported as
-# null (FLUX_TRAFFIC_BYTES_PER_FACE keeps the last measured figure, bytes per
-# face of a TGV 32^3 launch, for reference).
+# the ncu instruction counters of one capture of the kernel on TGV 32^3.
+# Later rewrites of the kernel (the Gauss-point polynomials as multiply-add
+# chains, the scales 1/rho and 1/h moved from the slope data into the slope
+# solves' constants) execute fewer flops for the same algorithm, so
+# `achieved` is the rate of that fixed work per Gauss point (algorithm-
+# equivalent flop), not of the flops the current kernel issues.  The DRAM
+# traffic of that capture no longer describes the current kernel and is
+# reported as null (FLUX_TRAFFIC_BYTES_PER_FACE keeps the last measured
+# figure, bytes per face of a TGV 32^3 launch, for reference).
 FLUX_FP64_FLOP_PER_GP = 3018.0
 FLUX_FP32_FLOP_PER_GP = 2769.0
 FLUX_TRAFFIC_BYTES_PER_FACE = {"fp64": 14.300e6 / 33792, "mixed": 7.209e6 / 33792}
@@ -216,6 +218,9 @@ def run_gpu(args, rank, world, local, dist):
                                           if FLUX_TRAFFIC_CURRENT else
                                           "null: the kernel changed after its last ncu capture (which read "
                                           f"{FLUX_TRAFFIC_BYTES_PER_FACE[prec_name]:.0f} B per face)"),
+                         "work_note": (f"{flop_gp:.0f} flop per Gauss point, the executed count of an ncu "
+                                       "capture of an earlier build of the kernel; the current build executes "
+                                       "fewer for the same algorithm (algorithm-equivalent flop)"),
                          "kernel": "k_face_flux", "pipe": "fp64" if prec_name == "fp64" else "fp32",
                          "peak_source": "derived: 152 SMs x 2070 MHz x (4 FP64 | 256 FP32) flop/clk/SM"},
             "t_reached": t_now,

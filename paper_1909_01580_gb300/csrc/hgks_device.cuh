@@ -307,6 +307,7 @@ template <typename R> struct Prim {
     R th;  // 1/(2 lam)
     R q2;  // U^2 + (K+3)/(2 lam)
     R c4;  // 4 lam^2/(K+3)
+    R H;   // (rho E + p)/rho
 };
 
 // iKp3 = 1/(K+3)
@@ -318,8 +319,12 @@ template <typename R> HK_HD Prim<R> primitive(const R Wc[5], R gamma, R Kp3, R i
     s.U = Wc[1] * s.ir;
     s.V = Wc[2] * s.ir;
     s.W = Wc[3] * s.ir;
-    R eint = Wc[4] - R(0.5) * (Wc[1] * s.U + Wc[2] * s.V + Wc[3] * s.W);
+    R m2 = Wc[1] * s.U;
+    m2 += Wc[2] * s.V;
+    m2 += Wc[3] * s.W;
+    const R eint = Wc[4] - R(0.5) * m2;
     s.p = (gamma - R(1)) * eint;
+    s.H = (Wc[4] + s.p) * s.ir;
     // rho E = rho |U|^2/2 + (K+3) rho/(4 lam)
     s.lam = Kp3 * Wc[0] / (R(4) * eint);
     s.th = R(2) * iKp3 * eint * s.ir;
@@ -328,22 +333,24 @@ template <typename R> HK_HD Prim<R> primitive(const R Wc[5], R gamma, R Kp3, R i
     return s;
 }
 
-// Solve <(a . psi') psi'> = b for a Maxwellian with velocity (U, 0, 0) and
-// lam (the closed form in peculiar velocity, tangential velocities zero).
-template <typename R> HK_HD void micro_slope_u(const Prim<R> &s, const R b[5], R a[5])
+// Solve <(a . psi') psi'> = sc b for a Maxwellian with velocity (U, 0, 0)
+// and lam (the closed form in peculiar velocity, tangential velocities zero).
+// The solution is linear in the data, so the scale sc (1/rho, and the
+// gradient units) multiplies the Maxwellian's constants, which the calls
+// with one scale share, instead of the five data values of every call.
+template <typename R> HK_HD void micro_slope_u(const Prim<R> &s, const R b[5], R sc, R a[5])
 {
     const R r1 = b[1] - s.U * b[0];
-    // a4 = c4 (2 b4 - q2 b0 - 2 U r1); the products of the Maxwellian's
-    // constants are shared between the calls for one Maxwellian
-    R e = (R(2) * s.c4) * b[4];
-    e -= (s.c4 * s.q2) * b[0];
-    e -= (R(2) * s.c4 * s.U) * r1;
+    // a4 = c4 (2 b4 - q2 b0 - 2 U r1) sc
+    R e = (R(2) * s.c4 * sc) * b[4];
+    e -= (s.c4 * s.q2 * sc) * b[0];
+    e -= (R(2) * s.c4 * s.U * sc) * r1;
     a[4] = e;
-    const R l2 = R(2) * s.lam;
-    a[1] = l2 * r1 - s.U * a[4];
-    a[2] = l2 * b[2];
-    a[3] = l2 * b[3];
-    e = b[0] - s.U * a[1];
+    const R kl = R(2) * s.lam * sc;
+    a[1] = kl * r1 - s.U * a[4];
+    a[2] = kl * b[2];
+    a[3] = kl * b[3];
+    e = sc * b[0] - s.U * a[1];
     e -= (R(0.5) * s.q2) * a[4];
     a[0] = e;
 }
@@ -351,14 +358,16 @@ template <typename R> HK_HD void micro_slope_u(const Prim<R> &s, const R b[5], R
 // out += dF_i, the derivative of the Euler flux in direction i for the
 // derivative d of the conservative variables.  For a Maxwellian g_W and the
 // slope a with (a . psi) g = dg/dx_i this equals <u_i (a . psi) psi g>, the
-// moment the compatibility condition needs, in closed form.
-template <int I, typename R>
-HK_HD void euler_dflux(const Prim<R> &s, const R Wc[5], R ir, R gm1, const R d[5], R out[5])
+// moment the compatibility condition needs, in closed form.  With
+// delta_j = d(rho u_j) - u_j d rho = rho du_j:
+//   d(rho u_j u_i) = d(rho u_i) u_j + u_i delta_j,
+//   d(u_i (rho E + p)) = delta_i H + u_i (d(rho E) + dp),  H = (rho E + p)/rho.
+template <int I, typename R> HK_HD void euler_dflux(const Prim<R> &s, R gm1, const R d[5], R out[5])
 {
     const R u[3] = {s.U, s.V, s.W};
-    R du[3];
+    R dl[3];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) du[j] = (d[1 + j] - u[j] * d[0]) * ir;
+    for (int j = 0; j < 3; ++j) dl[j] = d[1 + j] - u[j] * d[0];
     // dp = (gamma - 1)(d4 + |u|^2/2 d0 - u . d), as a chain of multiply-adds
     R e = d[4];
     e += (R(0.5) * (s.U * s.U + s.V * s.V + s.W * s.W)) * d[0];
@@ -371,12 +380,12 @@ HK_HD void euler_dflux(const Prim<R> &s, const R Wc[5], R ir, R gm1, const R d[5
     for (int j = 0; j < 3; ++j) {
         R o = out[1 + j];
         o += d[1 + I] * u[j];
-        o += Wc[1 + I] * du[j];
+        o += u[I] * dl[j];
         out[1 + j] = o;
     }
     out[1 + I] += dp;
     R o4 = out[4];
-    o4 += du[I] * (Wc[4] + s.p);
+    o4 += dl[I] * s.H;
     o4 += u[I] * (d[4] + dp);
     out[4] = o4;
 }
@@ -393,9 +402,11 @@ HK_HD void euler_dflux(const Prim<R> &s, const R Wc[5], R ir, R gm1, const R d[5
 // right-hand sides sum_i <u_i (a_i . psi) psi> are the Euler flux
 // derivatives (euler_dflux); both are exact rewritings of the moments.
 // ---------------------------------------------------------------------------
+// gs: the physical gradient is gs times dWl, dWr (1 for physical
+// gradients; 1/h for derivatives in the scaled frame of a cube of edge h).
 template <typename R>
 HK_HD void gks_flux(const R Wl[5], const R dWl[3][5], const R Wr[5], const R dWr[3][5],
-                                         const Scheme &S, R dt, R F[5], R dF[5])
+                                         const Scheme &S, R dt, R F[5], R dF[5], R gs = R(1))
 {
     const FluxK<R> C = fluxk<R>(S);
     const R gamma = C.gamma, K = C.K, Kp3 = C.Kp3, gm1 = C.gm1, iKp3 = C.iKp3;
@@ -415,26 +426,25 @@ HK_HD void gks_flux(const R Wl[5], const R dWl[3][5], const R Wr[5], const R dWr
         const R(*dW)[5] = side ? dWr : dWl;
         const Prim<R> s = primitive(Wc, gamma, Kp3, iKp3);
         pside[side] = s.p;
-        const R ir = s.ir;
-        // time slope data: b_A = -(1/rho) sum_i dF_i
+        // slope data per unit density: b_i = gs dW_i / rho, and for the time
+        // slope b_A = -(gs/rho) sum_i dF_i(dW_i); the scales go to the solves
+        const R irg = s.ir * gs;
         R bA[5] = {R(0), R(0), R(0), R(0), R(0)};
-        euler_dflux<0>(s, Wc, ir, gm1, dW[0], bA);
-        euler_dflux<1>(s, Wc, ir, gm1, dW[1], bA);
-        euler_dflux<2>(s, Wc, ir, gm1, dW[2], bA);
+        euler_dflux<0>(s, gm1, dW[0], bA);
+        euler_dflux<1>(s, gm1, dW[1], bA);
+        euler_dflux<2>(s, gm1, dW[2], bA);
         // spatial and time slopes in the tangentially moving frame
         R a[3][5], A[5];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             R b[5];
 #pragma unroll
-            for (int k = 0; k < 5; ++k) b[k] = dW[i][k] * ir;
+            for (int k = 0; k < 5; ++k) b[k] = dW[i][k];
             boost_in(s.V, s.W, b);
-            micro_slope_u(s, b, a[i]);
+            micro_slope_u(s, b, irg, a[i]);
         }
-#pragma unroll
-        for (int k = 0; k < 5; ++k) bA[k] = -bA[k] * ir;
         boost_in(s.V, s.W, bA);
-        micro_slope_u(s, bA, A);
+        micro_slope_u(s, bA, -irg, A);
         // u on the half line of this side
         BMom<R> B;
         mom_half_1d(s.U, s.lam, s.th, side ? R(-1) : R(1), B.m);
@@ -508,27 +518,25 @@ HK_HD void gks_flux(const R Wl[5], const R dWl[3][5], const R Wr[5], const R dWr
     // equilibrium state at the interface and its slopes
     const Prim<R> s0 = primitive(W0, gamma, Kp3, iKp3);
     const R ir0 = s0.ir;
+    // S0b = sum_i <u_i (abar_i . psi) psi g0> (density rho0 included)
     R abar[3][5], Abar[5], S0b[5] = {R(0), R(0), R(0), R(0), R(0)};
-    euler_dflux<0>(s0, W0, ir0, gm1, dW0[0], S0b);
-    euler_dflux<1>(s0, W0, ir0, gm1, dW0[1], S0b);
-    euler_dflux<2>(s0, W0, ir0, gm1, dW0[2], S0b);
+    euler_dflux<0>(s0, gm1, dW0[0], S0b);
+    euler_dflux<1>(s0, gm1, dW0[1], S0b);
+    euler_dflux<2>(s0, gm1, dW0[2], S0b);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         R b[5];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) b[k] = dW0[i][k] * ir0;
+        for (int k = 0; k < 5; ++k) b[k] = dW0[i][k];
         boost_in(s0.V, s0.W, b);
-        micro_slope_u(s0, b, abar[i]);
+        micro_slope_u(s0, b, ir0, abar[i]);
     }
     {
         R b[5];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            S0b[k] *= ir0;  // sum_i <u_i (abar_i . psi) psi> per unit density
-            b[k] = -S0b[k];
-        }
+        for (int k = 0; k < 5; ++k) b[k] = S0b[k];
         boost_in(s0.V, s0.W, b);
-        micro_slope_u(s0, b, Abar);
+        micro_slope_u(s0, b, -ir0, Abar);
     }
     BMom<R> B0;
     {
@@ -608,7 +616,8 @@ HK_HD void gks_flux(const R Wl[5], const R dWl[3][5], const R Wr[5], const R dWr
         // S the psi-moments of the same terms (S of the g0 A-term is -S0b).
         R uu = R(0.5) * (s0.U * s0.U + s0.V * s0.V + s0.W * s0.W);
         R Sx[5], Sd[5];
-        const R c03 = c0 + c3, c12 = s0.rho * (c1 - c2), d03 = d0 + d3, d12 = s0.rho * (d1 - d2);
+        // S0b carries the density rho0 already
+        const R c03 = c0 + c3, c12 = c1 - c2, d03 = d0 + d3, d12 = d1 - d2;
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             R e = c03 * Sa[k];

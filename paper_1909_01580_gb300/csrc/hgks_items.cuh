@@ -374,8 +374,8 @@ __device__ __forceinline__ void positivity_item(const double *__restrict__ Q, R 
 // the faces computes a clamped face and writes nothing.
 // ---------------------------------------------------------------------------
 template <typename R, int D>
-__device__ __forceinline__ void eval_side(const R *__restrict__ coef, long long stride, long long ci, const Geo &g,
-                                          R xd, R xa, R xb, R W[5], R dW[3][5])
+__device__ __forceinline__ void eval_side(const R *__restrict__ coef, long long stride, long long ci, R xd, R xa,
+                                          R xb, R W[5], R dW[3][5])
 {
     // at a face Gauss point the face-normal coordinate is xd = +-1/2 and the
     // tangential ones are +-1/(2 sqrt 3), so the zero-mean tangential squares
@@ -384,9 +384,9 @@ __device__ __forceinline__ void eval_side(const R *__restrict__ coef, long long 
     constexpr int DA = D + A == 1 ? 6 : (D + A == 2 ? 7 : 8);
     constexpr int DB = D + B == 1 ? 6 : (D + B == 2 ? 7 : 8);
     constexpr int AB = A + B == 1 ? 6 : (A + B == 2 ? 7 : 8);
-    const R ih = R(g.inv_h);
     // point factors shared by the five variables; the sums below are chains
-    // of multiply-adds
+    // of multiply-adds.  The gradients stay in the scaled frame (derivatives
+    // per cell edge): the flux takes the factor 1/h with its slope data.
     const R xab = xa * xb, xd2 = R(2) * xd, xa2 = R(2) * xa, xb2 = R(2) * xb;
     R val[5], grad[5][3];
 #pragma unroll
@@ -405,17 +405,17 @@ __device__ __forceinline__ void eval_side(const R *__restrict__ coef, long long 
         e += c[3 + D] * xd2;
         e += c[DA] * xa;
         e += c[DB] * xb;
-        grad[v][D] = e * ih;
+        grad[v][D] = e;
         e = c[A];
         e += c[3 + A] * xa2;
         e += c[DA] * xd;
         e += c[AB] * xb;
-        grad[v][A] = e * ih;
+        grad[v][A] = e;
         e = c[B];
         e += c[3 + B] * xb2;
         e += c[DB] * xd;
         e += c[AB] * xa;
-        grad[v][B] = e * ih;
+        grad[v][B] = e;
     }
     // local frame: local axis l is global axis (D + l) % 3
     W[0] = val[0];
@@ -457,14 +457,14 @@ __device__ __forceinline__ void flux_item(const R *__restrict__ coef, double *__
     const R xb = (gp & 1) ? R(GAUSS_S) : R(-GAUSS_S);
     R Wl[5], dWl[3][5], Wr[5], dWr[3][5];
     if (CH) {
-        eval_side<R, D>(coef, nface, face, g, R(0.5), xa, xb, Wl, dWl);
-        eval_side<R, D>(coef + 50 * nface, nface, face, g, R(-0.5), xa, xb, Wr, dWr);
+        eval_side<R, D>(coef, nface, face, R(0.5), xa, xb, Wl, dWl);
+        eval_side<R, D>(coef + 50 * nface, nface, face, R(-0.5), xa, xb, Wr, dWr);
     } else {
-        eval_side<R, D>(coef, g.cstride, cidx(g, il, jl, kl), g, R(0.5), xa, xb, Wl, dWl);
-        eval_side<R, D>(coef, g.cstride, cidx(g, i, j, k), g, R(-0.5), xa, xb, Wr, dWr);
+        eval_side<R, D>(coef, g.cstride, cidx(g, il, jl, kl), R(0.5), xa, xb, Wl, dWl);
+        eval_side<R, D>(coef, g.cstride, cidx(g, i, j, k), R(-0.5), xa, xb, Wr, dWr);
     }
     R F[5], dF[5];
-    gks_flux<R>(Wl, dWl, Wr, dWr, S, R(dt), F, dF);
+    gks_flux<R>(Wl, dWl, Wr, dWr, S, R(dt), F, dF, R(g.inv_h));
     // back to the global frame, Gauss weight 1/4, sum of the 4 lanes in the
     // working precision; the face value is stored in FP64
     R f[10];

@@ -3,7 +3,9 @@
 // 40 values (left state, its three directional derivatives, right state,
 // its derivatives, local frame) from a binary file and writes n x 10 values
 // (F, dF/dt) to another.  Usage: flux_host_check R dt gamma mu Pr tau_eps
-// tau_C n in out, R = 64 or 32.
+// tau_C n in out [gs], R = 64 or 32; with gs the gradients are passed as
+// dW/gs together with the gradient scale gs (the uniform mesh's scaled
+// frame), which must give the same flux.
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -11,7 +13,8 @@
 #include "hgks_device.cuh"
 
 template <typename R>
-static void run(const hk::Scheme &S, double dt, int n, const std::vector<double> &in, std::vector<double> &out)
+static void run(const hk::Scheme &S, double dt, double gs, int n, const std::vector<double> &in,
+                std::vector<double> &out)
 {
     for (int p = 0; p < n; ++p) {
         const double *x = in.data() + 40 * (size_t)p;
@@ -19,10 +22,10 @@ static void run(const hk::Scheme &S, double dt, int n, const std::vector<double>
         for (int s = 0; s < 2; ++s)
             for (int v = 0; v < 5; ++v) {
                 W[s][v] = R(x[20 * s + v]);
-                for (int e = 0; e < 3; ++e) dW[s][e][v] = R(x[20 * s + 5 + 5 * e + v]);
+                for (int e = 0; e < 3; ++e) dW[s][e][v] = R(x[20 * s + 5 + 5 * e + v] / gs);
             }
         R F[5], dF[5];
-        hk::gks_flux<R>(W[0], dW[0], W[1], dW[1], S, R(dt), F, dF);
+        hk::gks_flux<R>(W[0], dW[0], W[1], dW[1], S, R(dt), F, dF, R(gs));
         for (int v = 0; v < 5; ++v) {
             out[10 * (size_t)p + v] = double(F[v]);
             out[10 * (size_t)p + 5 + v] = double(dF[v]);
@@ -32,7 +35,8 @@ static void run(const hk::Scheme &S, double dt, int n, const std::vector<double>
 
 int main(int argc, char **argv)
 {
-    if (argc != 11) return 2;
+    if (argc != 11 && argc != 12) return 2;
+    const double gs = argc == 12 ? atof(argv[11]) : 1.0;
     const int prec = atoi(argv[1]);
     const double dt = atof(argv[2]);
     hk::Scheme S{};
@@ -52,8 +56,8 @@ int main(int argc, char **argv)
     FILE *f = fopen(argv[9], "rb");
     if (!f || fread(in.data(), sizeof(double), in.size(), f) != in.size()) return 3;
     fclose(f);
-    if (prec == 32) run<float>(S, dt, n, in, out);
-    else run<double>(S, dt, n, in, out);
+    if (prec == 32) run<float>(S, dt, gs, n, in, out);
+    else run<double>(S, dt, gs, n, in, out);
     f = fopen(argv[10], "wb");
     if (!f || fwrite(out.data(), sizeof(double), out.size(), f) != out.size()) return 4;
     fclose(f);

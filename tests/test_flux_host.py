@@ -30,24 +30,28 @@ def exe(tmp_path_factory):
     return str(out)
 
 
-def _host_flux(exe, tmp, inp, dt, gamma, mu, Pr, bits):
+def _host_flux(exe, tmp, inp, dt, gamma, mu, Pr, bits, gs=None):
     fin, fout = tmp / "in.bin", tmp / "out.bin"
     np.ascontiguousarray(inp, dtype=np.float64).tofile(fin)
-    r = subprocess.run([exe, str(bits), repr(dt), repr(gamma), repr(mu), repr(Pr), "0.01", "1.0",
-                        str(len(inp)), str(fin), str(fout)], capture_output=True, text=True, timeout=60)
+    args = [exe, str(bits), repr(dt), repr(gamma), repr(mu), repr(Pr), "0.01", "1.0", str(len(inp)), str(fin),
+            str(fout)] + ([repr(gs)] if gs is not None else [])
+    r = subprocess.run(args, capture_output=True, text=True, timeout=60)
     assert r.returncode == 0, (r.returncode, r.stderr)
     out = np.fromfile(fout, dtype=np.float64).reshape(len(inp), 10)
     return out[:, :5], out[:, 5:]
 
 
 @pytest.mark.parametrize("mu,Pr", [(0.0, 1.0), (0.02, 1.0), (0.02, 0.72)])
-def test_host_flux_fp64_matches_oracle(exe, tmp_path, mu, Pr):
+@pytest.mark.parametrize("gs", [None, 16.0])
+def test_host_flux_fp64_matches_oracle(exe, tmp_path, mu, Pr, gs):
+    """gs: gradients passed in the scaled frame of a cube of edge 1/16 with
+    the gradient scale, as the uniform mesh's face kernel passes them."""
     rng = np.random.default_rng(11)
     inp = random_point_inputs(rng, 48)
     dt = 0.05
     cfg = oracle.make_cfg((4, 4, 4), mu=mu, Pr=Pr)
     Fo, dFo = oracle.point_flux(cfg, inp, dt)
-    F, dF = _host_flux(exe, tmp_path, inp, dt, 1.4, mu, Pr, 64)
+    F, dF = _host_flux(exe, tmp_path, inp, dt, 1.4, mu, Pr, 64, gs)
     assert max_rel(F, Fo, axis_vars=1) <= 1e-12
     assert max_rel(dF, dFo, axis_vars=1) <= 1e-9
 
