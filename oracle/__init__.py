@@ -91,6 +91,11 @@ def make_cfg(n, lo=(0.0, 0.0, 0.0), hi=(2.0, 2.0, 2.0), *, gamma=1.4, mu=0.0, Pr
     return c
 
 
+# rate(ctx, stage, y, L, dL) of orc_two_stage
+RATE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double))
+
+
 def lib():
     global _lib
     with _lock:
@@ -128,6 +133,8 @@ def lib():
             L.orc_stencils_sprime.argtypes = [P(ctypes.c_int), P(ctypes.c_int)]
             L.orc_char_basis.restype = ctypes.c_int
             L.orc_stencils.restype = None
+            L.orc_two_stage.argtypes = [ctypes.c_long, dp, D, RATE_FN, ctypes.c_void_p]
+            L.orc_two_stage.restype = ctypes.c_int
             L.orc_threads_used.argtypes = [cp]
             L.orc_threads_used.restype = ctypes.c_int
             _lib = L
@@ -252,6 +259,27 @@ def step(cfg: Cfg, q, t: float, nsteps: int, cfl: float = 0.35, dt_fixed: float 
     if rc != 0:
         raise RuntimeError("oracle step failed")
     return q, tt.value, done.value, v
+
+
+def two_stage(y, dt: float, nsteps: int, rate):
+    """Advance y by nsteps steps of the oracle's two-stage fourth-order
+    routine (the one every scheme step runs through), with the rate pair
+    supplied from Python: rate(stage, y) -> (L, dL/dt), arrays like y."""
+    y = _f64(y).copy().ravel()
+    n = y.size
+
+    def cb(_ctx, stage, yp, Lp, dLp):
+        yy = np.ctypeslib.as_array(yp, shape=(n,)).copy()
+        L, dL = rate(int(stage), yy)
+        np.ctypeslib.as_array(Lp, shape=(n,))[:] = L
+        np.ctypeslib.as_array(dLp, shape=(n,))[:] = dL
+        return 0
+
+    fn = RATE_FN(cb)
+    for _ in range(nsteps):
+        if lib().orc_two_stage(n, _dp(y), float(dt), fn, None) != 0:
+            raise RuntimeError("oracle two-stage step failed")
+    return y
 
 
 def moments_1d(U: float, lam: float, side: int) -> np.ndarray:

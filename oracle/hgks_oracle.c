@@ -1678,67 +1678,97 @@ int orc_volumes(const orc_cfg *c, double t, double *vol)
     return 0;
 }
 
-/* Two-stage fourth-order time stepping (Sec. 3) on a fixed mesh:
- *   Q*      = Q^n + dt/2 L(Q^n) + dt^2/8 dL/dt(Q^n)
- *   Q^{n+1} = Q^n + dt L(Q^n) + dt^2/6 (dL/dt(Q^n) + 2 dL/dt(Q*))
- * Reading: the intermediate stage reuses the same dt, with tau from the
- * pressures of Q*.  On a moving mesh (Remark 2) the same formula advances
- * |Omega| Q with geometry frozen at the start of each stage (t_n, then
- * t_n + dt/2), and the volume that divides it is advanced by the same
- * formula from the grid's swept-volume rate (discrete geometric
- * conservation law).  dt_fixed > 0 fixes dt; otherwise the CFL step is
- * clipped to t_end.  vol (optional, in/out) carries those volumes. */
+/* One step of the two-stage fourth-order method (Sec. 3) for
+ * dy/dt = L(y) with the rate pair (L, dL/dt) supplied by `rate`:
+ *   y*      = y^n + dt/2 L(y^n) + dt^2/8 dL/dt(y^n)
+ *   y^{n+1} = y^n + dt L(y^n) + dt^2/6 (dL/dt(y^n) + 2 dL/dt(y*))
+ * rate(ctx, stage, y, L, dL) evaluates the pair at y^n (stage 0) and at y*
+ * (stage 1); the intermediate stage reuses the same dt. */
+typedef int (*orc_rate_fn)(void *ctx, int stage, const double *y, double *L, double *dL);
+
+int orc_two_stage(long n, double *y, double dt, orc_rate_fn rate, void *ctx)
+{
+    double *L1 = malloc(n * sizeof(double)), *dL1 = malloc(n * sizeof(double));
+    double *L2 = malloc(n * sizeof(double)), *dL2 = malloc(n * sizeof(double));
+    double *ys = malloc(n * sizeof(double));
+    int rc = -1;
+    if (!L1 || !dL1 || !L2 || !dL2 || !ys) goto out;
+    if ((rc = rate(ctx, 0, y, L1, dL1))) goto out;
+    for (long i = 0; i < n; ++i) ys[i] = y[i] + 0.5 * dt * L1[i] + 0.125 * dt * dt * dL1[i];
+    if ((rc = rate(ctx, 1, ys, L2, dL2))) goto out;
+    for (long i = 0; i < n; ++i) y[i] = y[i] + dt * L1[i] + dt * dt / 6.0 * (dL1[i] + 2.0 * dL2[i]);
+out:
+    free(L1); free(dL1); free(L2); free(dL2); free(ys);
+    return rc;
+}
+
+/* The scheme's rate pair for orc_two_stage.  y = (|Omega| Q [5][N], |Omega| [N]);
+ * L = (-sum of face fluxes, swept-volume rate), dL/dt = (its time derivative, 0):
+ * the geometry of a stage is frozen at its start (Remark 2), so the volume
+ * rate has no time derivative within a stage. */
+typedef struct {
+    const orc_cfg *c;
+    size_t nint;
+    double t, dt;
+    const double *q0;  /* Q^n itself, used at stage 0 */
+    double *qs;        /* the intermediate state Q* = (|Omega| Q)* / |Omega|* */
+} step_ctx;
+
+static int scheme_rate(void *vctx, int stage, const double *y, double *L, double *dL)
+{
+    step_ctx *x = (step_ctx *)vctx;
+    const size_t nint = x->nint;
+    const double *q = x->q0;
+    if (stage == 1) {
+        for (size_t i = 0; i < nint; ++i)
+            for (int v = 0; v < NV; ++v) x->qs[(size_t)v * nint + i] = y[(size_t)v * nint + i] / y[NV * nint + i];
+        q = x->qs;
+    }
+    orc_geom G;
+    if (geom_build(x->c, x->t + (stage ? 0.5 * x->dt : 0.0), &G)) return -1;
+    int rc = residuals(x->c, &G, q, x->dt, L, dL, L + NV * nint, -1, NULL);
+    geom_free(&G);
+    for (size_t i = 0; i < nint; ++i) dL[NV * nint + i] = 0.0;
+    return rc;
+}
+
+/* Time stepping of the scheme (Sec. 3): each step is orc_two_stage on
+ * (|Omega| Q, |Omega|).  Reading: the intermediate stage reuses the same
+ * dt, with tau from the pressures of Q*.  On a moving mesh (Remark 2) the
+ * two-stage formula advances |Omega| Q with geometry frozen at the start of
+ * each stage (t_n, then t_n + dt/2), and the volume that divides it is
+ * advanced by the same formula from the grid's swept-volume rate (discrete
+ * geometric conservation law); on a fixed mesh that rate is zero.
+ * dt_fixed > 0 fixes dt; otherwise the CFL step is clipped to t_end.
+ * vol (optional, in/out) carries those volumes. */
 int orc_step(const orc_cfg *c, double *q, double *t, int nsteps, double cfl, double dt_fixed, double t_end,
              double *vol_io, int *steps_done)
 {
     size_t nint = (size_t)c->n[0] * c->n[1] * c->n[2];
-    double *R1 = malloc(nint * NV * sizeof(double)), *dR1 = malloc(nint * NV * sizeof(double));
-    double *R2 = malloc(nint * NV * sizeof(double)), *dR2 = malloc(nint * NV * sizeof(double));
+    double *y = malloc(nint * (NV + 1) * sizeof(double));
     double *qs = malloc(nint * NV * sizeof(double));
-    double *V1 = malloc(nint * sizeof(double)), *V2 = malloc(nint * sizeof(double));
-    double *vol = malloc(nint * sizeof(double)), *vols = malloc(nint * sizeof(double));
+    double *vol = y ? y + NV * nint : NULL;
     int rc = 0, done = 0;
-    if (!R1 || !dR1 || !R2 || !dR2 || !qs || !V1 || !V2 || !vol || !vols) { rc = -1; goto out; }
+    if (!y || !qs) { rc = -1; goto out; }
     if (vol_io && c->mesh == 2) memcpy(vol, vol_io, nint * sizeof(double));
     else if (orc_volumes(c, *t, vol)) { rc = -1; goto out; }
     for (int n = 0; n < nsteps; ++n) {
         double dt = dt_fixed > 0.0 ? dt_fixed : orc_cfl_dt(c, q, *t, cfl);
         if (dt_fixed <= 0.0 && *t + dt > t_end) dt = t_end - *t;
         if (!(dt > 0.0)) break;
-        orc_geom G;
-        /* stage 1 at t_n */
-        if (geom_build(c, *t, &G)) { rc = -1; goto out; }
-        rc = residuals(c, &G, q, dt, R1, dR1, V1, -1, NULL);
-        geom_free(&G);
-        if (rc) goto out;
-        for (size_t i = 0; i < nint; ++i) {
-            double vs = vol[i] + 0.5 * dt * V1[i];
-            vols[i] = vs;
-            for (int v = 0; v < NV; ++v) {
-                size_t x = (size_t)v * nint + i;
-                qs[x] = (vol[i] * q[x] + 0.5 * dt * R1[x] + 0.125 * dt * dt * dR1[x]) / vs;
-            }
-        }
-        /* stage 2 at t_n + dt/2 */
-        if (geom_build(c, *t + 0.5 * dt, &G)) { rc = -1; goto out; }
-        rc = residuals(c, &G, qs, dt, R2, dR2, V2, -1, NULL);
-        geom_free(&G);
-        if (rc) goto out;
-        for (size_t i = 0; i < nint; ++i) {
-            double vn = vol[i] + dt * V1[i];
-            for (int v = 0; v < NV; ++v) {
-                size_t x = (size_t)v * nint + i;
-                q[x] = (vol[i] * q[x] + dt * R1[x] + dt * dt / 6.0 * (dR1[x] + 2.0 * dR2[x])) / vn;
-            }
-            vol[i] = vn;
-        }
+        for (size_t i = 0; i < nint; ++i)
+            for (int v = 0; v < NV; ++v) y[(size_t)v * nint + i] = vol[i] * q[(size_t)v * nint + i];
+        step_ctx x = {c, nint, *t, dt, q, qs};
+        if ((rc = orc_two_stage((long)(nint * (NV + 1)), y, dt, scheme_rate, &x))) goto out;
+        for (size_t i = 0; i < nint; ++i)
+            for (int v = 0; v < NV; ++v) q[(size_t)v * nint + i] = y[(size_t)v * nint + i] / vol[i];
         *t += dt;
         ++done;
     }
     if (vol_io) memcpy(vol_io, vol, nint * sizeof(double));
 out:
     if (steps_done) *steps_done = done;
-    free(R1); free(dR1); free(R2); free(dR2); free(qs); free(V1); free(V2); free(vol); free(vols);
+    free(y); free(qs);
     return rc;
 }
 
