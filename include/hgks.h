@@ -69,7 +69,7 @@ enum {
 
 /* Create a solver on the current CUDA device.
  *   grid    mesh and precision (see hgks_grid_t); cells must be cubes and
- *           every axis needs at least 2 cells.
+ *           every axis needs at least 2 cells (3 on an axis with a reflective side).
  *   gamma   ratio of specific heats; K = (5 - 3 gamma)/(gamma - 1) internal
  *           degrees of freedom of the Maxwellian (Sec. 3, BGK model).
  *   mu      dynamic viscosity.  mu = 0 selects the inviscid collision time
@@ -269,7 +269,7 @@ void hgks_batch_destroy(hgks_batch_t *b);
  * library call.
  *   grid, gamma, mu, Pr, bc  as for hgks_create.
  *   q      device pointer, the state [5][nz][ny][nx] FP64 (read only).
- *   dt     time step, > 0.
+ *   dt     time step, a positive finite number (else HGKS_E_INVALID).
  *   L, dLdt  device pointers [5][nz][ny][nx] FP64 (written).
  *   stream cudaStream_t (or NULL for the legacy default stream); the call is
  *          ordered on it and returns without synchronising.
@@ -289,6 +289,17 @@ int hgks_flux_noalloc(const hgks_grid_t *grid, double gamma, double mu, double P
 
 /* Kernel launches this handle has issued since creation (for accounting). */
 unsigned long long hgks_launch_count(const hgks_t *h);
+
+/* Measurement utility (the paper has no counterpart): the fused
+ * multiply-add rate of the current device in one precision, in TFLOP/s
+ * (2 flop per FMA), from independent FMA chains on every SM (one warm-up and
+ * one timed launch of about 50 ms, CUDA events on cuda_stream; NULL is the
+ * legacy default stream).  precision: HGKS_FP64 for the FP64 pipe,
+ * HGKS_MIXED for the FP32 pipe.  It is the measured denominator of the ALU
+ * roofline of the reconstruction and Gauss-point flux kernels.  Allocates
+ * and frees a few KB of device memory; synchronises cuda_stream.
+ * HGKS_E_INVALID for a bad precision or a NULL tflops. */
+int hgks_alu_peak(int precision, void *cuda_stream, double *tflops);
 
 /* Bytes of device memory this handle holds. */
 unsigned long long hgks_device_bytes(const hgks_t *h);

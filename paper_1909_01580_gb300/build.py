@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhgks.so")
-SOURCES = ["hgks_kernels.cu", "hgks_mapped.cu", "hgks_char.cu", "hgks_api.cu", "hgks_noalloc.cu", "hgks_batch.cu"]
+SOURCES = ["hgks_kernels.cu", "hgks_mapped.cu", "hgks_char.cu", "hgks_api.cu", "hgks_noalloc.cu", "hgks_batch.cu",
+           "hgks_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -prec-div=false / -prec-sqrt=false: FP32 division and square root of the
 # mixed path to within 2 ulp instead of correctly rounded (FP64 arithmetic is

@@ -174,10 +174,12 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
     if (!grid || !bc || !out) return fail(nullptr, HGKS_E_INVALID, "null argument%s");
     *out = nullptr;
     for (int d = 0; d < 3; ++d) {
-        // two ghost layers mirror or wrap at most two interior cells
+        // periodic ghosts wrap modulo n (2 cells suffice); the GHOST = 3
+        // reflective ghost layers mirror three interior cells
         if (grid->n[d] < 2 || grid->n[d] > HGKS_MAX_CELLS_PER_AXIS || !(grid->hi[d] > grid->lo[d]) ||
             (grid->n[d] < hk::GHOST && (bc[2 * d] == HGKS_BC_REFLECTIVE || bc[2 * d + 1] == HGKS_BC_REFLECTIVE)))
-            return fail(nullptr, HGKS_E_INVALID, "each axis needs at least 2 cells and hi > lo%s");
+            return fail(nullptr, HGKS_E_INVALID,
+                        "each axis needs at least 2 cells (3 with a reflective side) and hi > lo%s");
     }
     if (grid->mesh < 0 || grid->mesh > 2)
         return fail(nullptr, HGKS_E_INVALID, "mesh must be 0 (uniform), 1 (static mapped) or 2 (moving)%s");
@@ -623,7 +625,7 @@ extern "C" int hgks_step(hgks_t *h, int nsteps, double cfl, double dt_fixed, dou
 
 extern "C" int hgks_flux(hgks_t *h, double dt, double *L, double *dLdt, int on_device)
 {
-    if (!h || !L || !dLdt || !(dt > 0.0)) return HGKS_E_INVALID;
+    if (!h || !L || !dLdt || !(dt > 0.0) || !isfinite(dt)) return HGKS_E_INVALID;
     if (!h->have_state) return fail(h, HGKS_E_STATE, "no state loaded%s");
     const Geo &g = h->g;
     cudaStream_t s = h->stream;
@@ -704,7 +706,7 @@ extern "C" int hgks_reconstruct(hgks_t *h, double *coef, int *flag)
 extern "C" int hgks_point_flux(int n, const double *in, const double *ug, double dt, const double params[5],
                                int precision, double *F, double *dF)
 {
-    if (n < 0 || (n > 0 && (!in || !F || !dF || !params)) || !(dt > 0.0)) return HGKS_E_INVALID;
+    if (n < 0 || (n > 0 && (!in || !F || !dF || !params)) || !(dt > 0.0) || !isfinite(dt)) return HGKS_E_INVALID;
     if (precision != HGKS_FP64 && precision != HGKS_MIXED) return HGKS_E_INVALID;
     if (n == 0) return HGKS_OK;
     Scheme S;

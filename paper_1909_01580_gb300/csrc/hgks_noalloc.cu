@@ -66,14 +66,14 @@ static int scratch_address(void **out)
 extern "C" int hgks_flux_noalloc(const hgks_grid_t *grid, double gamma, double mu, double Pr, const int bc[6],
                                  const double *q, double dt, double *L, double *dLdt, void *stream)
 {
-    if (!grid || !bc || !q || !L || !dLdt || !(dt > 0.0)) {
-        hgks_internal_set_error("hgks_flux_noalloc: null buffer or dt <= 0");
+    if (!grid || !bc || !q || !L || !dLdt || !(dt > 0.0) || !isfinite(dt)) {
+        hgks_internal_set_error("hgks_flux_noalloc: null buffer, or dt not a positive finite number");
         return HGKS_E_INVALID;
     }
     for (int d = 0; d < 3; ++d) {
         if (grid->n[d] < 2 || grid->n[d] > HGKS_MAX_CELLS_PER_AXIS || !(grid->hi[d] > grid->lo[d]) ||
             (grid->n[d] < hk::GHOST && (bc[2 * d] == HGKS_BC_REFLECTIVE || bc[2 * d + 1] == HGKS_BC_REFLECTIVE))) {
-            hgks_internal_set_error("hgks_flux_noalloc: each axis needs at least 2 cells and hi > lo");
+            hgks_internal_set_error("hgks_flux_noalloc: each axis needs at least 2 cells (3 with a reflective side) and hi > lo");
             return HGKS_E_INVALID;
         }
         if ((bc[2 * d] == HGKS_BC_PERIODIC) != (bc[2 * d + 1] == HGKS_BC_PERIODIC)) {

@@ -30,7 +30,7 @@ HGKS_E_STATE = -6
 # every symbol include/hgks.h declares
 EXPORTS = ("hgks_create", "hgks_set_option", "hgks_set_state", "hgks_get_state", "hgks_step", "hgks_flux",
            "hgks_reconstruct", "hgks_point_flux", "hgks_set_timing", "hgks_get_timing", "hgks_launch_count",
-           "hgks_device_bytes", "hgks_last_error", "hgks_destroy", "hgks_flux_noalloc",
+           "hgks_device_bytes", "hgks_last_error", "hgks_destroy", "hgks_flux_noalloc", "hgks_alu_peak",
            "hgks_batch_create", "hgks_batch_footprint", "hgks_batch_add", "hgks_batch_remove", "hgks_batch_step",
            "hgks_batch_poll", "hgks_batch_get_state", "hgks_batch_tune", "hgks_batch_set_tuning",
            "hgks_batch_get_tuning", "hgks_batch_launch_count", "hgks_batch_last_error", "hgks_batch_destroy")
@@ -119,6 +119,8 @@ def load(build_if_missing: bool = True):
     L.hgks_launch_count.restype = ctypes.c_ulonglong
     L.hgks_device_bytes.argtypes = [vp]
     L.hgks_device_bytes.restype = ctypes.c_ulonglong
+    L.hgks_alu_peak.argtypes = [ctypes.c_int, vp, dp]
+    L.hgks_alu_peak.restype = ctypes.c_int
     L.hgks_last_error.argtypes = [vp]
     L.hgks_last_error.restype = ctypes.c_char_p
     L.hgks_destroy.argtypes = [vp]
@@ -254,6 +256,14 @@ def hgks_flux_noalloc(n, lo, hi, q, dt, L, dL, gamma=1.4, mu=0.0, Pr=1.0, bc=(0,
     st = None if stream is None else ctypes.c_void_p(int(stream))
     _check(load().hgks_flux_noalloc(ctypes.byref(g), float(gamma), float(mu), float(Pr), bcs, pq, float(dt), pl, pd,
                                     st))
+
+
+def hgks_alu_peak(precision, stream=None) -> float:
+    """Measured FMA rate (TFLOP/s) of the FP64 (HGKS_FP64) or FP32
+    (HGKS_MIXED) pipe of the current device."""
+    out = ctypes.c_double(0.0)
+    _check(load().hgks_alu_peak(int(precision), ctypes.c_void_p(stream), ctypes.byref(out)))
+    return out.value
 
 
 def hgks_launch_count(h) -> int:

@@ -137,12 +137,16 @@ def serve_fifo(reqs, precision=hgks.HGKS_FP64):
     return out
 
 
-def next_admission(waiting, resident_cells, policy="fifo", max_resident_cells=None):
+def next_admission(waiting, resident_cells, policy="fifo", max_resident_cells=None, now=None, age_limit=None):
     """Index into `waiting` (requests that have arrived, in arrival order) of
     the request to admit next, or None to wait.
       policy "fifo": the oldest request;
       policy "sjf":  the request with the least estimated work (cells x
-                     target steps), ties by arrival.
+                     target steps), ties by arrival;
+      policy "aged": least work first, except that a request that has waited
+                     longer than age_limit seconds at time `now` goes first
+                     (the oldest such request), which bounds how long the
+                     largest requests can be passed over.
     With max_resident_cells, a request is admitted only while the resident
     cells stay within the cap (always when nothing is resident), so that
     the batch holds enough work to fill the GPU without sharing it among
@@ -151,8 +155,13 @@ def next_admission(waiting, resident_cells, policy="fifo", max_resident_cells=No
         return None
     if policy == "fifo":
         k = 0
-    elif policy == "sjf":
+    elif policy in ("sjf", "aged"):
         k = min(range(len(waiting)), key=lambda i: (waiting[i].cells * waiting[i].steps_target, i))
+        if policy == "aged":
+            if now is None or age_limit is None:
+                raise ValueError("policy 'aged' needs now and age_limit")
+            if now - waiting[0].arrival > age_limit:
+                k = 0
     else:
         raise ValueError(f"unknown policy {policy}")
     if max_resident_cells is not None and resident_cells > 0 and \
@@ -162,7 +171,7 @@ def next_admission(waiting, resident_cells, policy="fifo", max_resident_cells=No
 
 
 def serve_batched(reqs, precision=hgks.HGKS_FP64, arena_bytes=4 << 30, max_instances=64, steps_per_poll=4,
-                  tuning=None, cfl=0.35, keep_results=True, policy="fifo", max_resident_cells=None):
+                  tuning=None, cfl=0.35, keep_results=True, policy="fifo", max_resident_cells=None, age_limit=None):
     """Continuous batching in real time: arrivals are released at their
     arrival times (relative to the start of the call), admitted by
     next_admission() when the arena and a slot are free, advanced together by
@@ -184,7 +193,8 @@ def serve_batched(reqs, precision=hgks.HGKS_FP64, arena_bytes=4 << 30, max_insta
             waiting.append(pending.pop(0))
         # admit by the policy while the choice fits the arena
         while waiting:
-            k = next_admission(waiting, sum(r.cells for r in by_slot.values()), policy, max_resident_cells)
+            k = next_admission(waiting, sum(r.cells for r in by_slot.values()), policy, max_resident_cells,
+                               now=now, age_limit=age_limit)
             if k is None:
                 break
             r = waiting[k]

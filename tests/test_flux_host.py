@@ -56,11 +56,14 @@ def test_host_flux_fp64_matches_oracle(exe, tmp_path, mu, Pr, gs):
     assert max_rel(dF, dFo, axis_vars=1) <= 1e-9
 
 
-def test_host_flux_fp32_within_the_mixed_tolerance(exe, tmp_path):
+@pytest.mark.parametrize("gs", [None, 16.0, 128.0 / (2.0 * np.pi)])
+def test_host_flux_fp32_within_the_mixed_tolerance(exe, tmp_path, gs):
+    """gs as above; 128/(2 pi) is the scale 1/h of the TGV 128^3 mesh, which
+    the mixed face kernel folds into the FP32 constants of its slope solves."""
     rng = np.random.default_rng(13)
     inp = random_point_inputs(rng, 48)
     dt = 0.05
     cfg = oracle.make_cfg((4, 4, 4), mu=0.02, Pr=0.72)
     Fo, dFo = oracle.point_flux(cfg, inp, dt)
-    F, dF = _host_flux(exe, tmp_path, inp, dt, 1.4, 0.02, 0.72, 32)
+    F, dF = _host_flux(exe, tmp_path, inp, dt, 1.4, 0.02, 0.72, 32, gs)
     assert max_rel(F, Fo, axis_vars=1) <= 2e-5

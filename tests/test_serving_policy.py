@@ -27,3 +27,13 @@ def test_cap_on_resident_cells():
     assert next_admission(w, 500, "sjf", max_resident_cells=1000) is None
     assert next_admission(w, 10_000, "sjf", max_resident_cells=200_000) == 0
     assert next_admission([], 0, "fifo") is None
+
+
+def test_aged_least_work_first_lets_an_old_request_go_first():
+    w = [_req(0, 96, 100, 0.0), _req(1, 24, 20, 0.5), _req(2, 32, 20, 0.6)]
+    # young queue: least work first
+    assert next_admission(w, 0, "aged", now=1.0, age_limit=2.0) == 1
+    # the oldest request has waited past the limit: it goes first
+    assert next_admission(w, 0, "aged", now=2.5, age_limit=2.0) == 0
+    # the cap still applies to it
+    assert next_admission(w, 50_000, "aged", max_resident_cells=100_000, now=2.5, age_limit=2.0) is None

@@ -81,3 +81,16 @@ def test_noalloc_refuses_grid_beyond_its_scratch():
         hgks.hgks_flux_noalloc(n, (0, 0, 0), (1, 1, 1), q, 1e-3, L, dL)
     assert e.value.code == hgks.HGKS_E_INVALID
     assert "bytes of scratch" in str(e.value)
+
+
+def test_noalloc_refuses_a_time_step_that_is_not_finite():
+    import torch
+    hgks.load()
+    n = (8, 8, 8)
+    q = torch.from_numpy(W.density_advection(n)).cuda()
+    L = torch.zeros_like(q)
+    dL = torch.zeros_like(q)
+    for dt in (float("inf"), float("nan"), 0.0, -1e-3):
+        with pytest.raises(hgks.HgksError) as e:
+            hgks.hgks_flux_noalloc(n, (0, 0, 0), (2, 2, 2), q, dt, L, dL)
+        assert e.value.code == hgks.HGKS_E_INVALID
