@@ -218,8 +218,10 @@ unsigned long long hgks_batch_footprint(const hgks_grid_t *grid);
 /* Admit an instance: grid/gamma/mu/Pr/bc as for hgks_create (grid->precision
  * must equal the batch's), q its initial state ([5][nz][ny][nx] FP64 host),
  * t0 its time, t_end its end time, cfl its CFL number.  *slot receives its
- * slot.  HGKS_E_NOMEM when no slot or not enough free arena is left.
- * Synchronises the batch stream. */
+ * slot.  HGKS_E_NOMEM when no slot or not enough free arena is left;
+ * HGKS_E_NONPHYSICAL (nothing admitted, the resident instances untouched)
+ * when q holds a non-finite value or a cell with non-positive density or
+ * pressure.  Synchronises the batch stream. */
 int hgks_batch_add(hgks_batch_t *b, const hgks_grid_t *grid, double gamma, double mu, double Pr, const int bc[6],
                    const double *q, double t0, double t_end, double cfl, int *slot);
 

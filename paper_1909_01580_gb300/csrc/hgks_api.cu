@@ -26,7 +26,7 @@ struct hgks {
     bool own_stream;
     int device;
     double *Qn, *Qs, *Wacc;      // padded Q^n, padded Q*, accumulator / staging [5][ncell]
-    void *coef;                  // [NCOEF][cstride] in the working precision
+    void *coef;                  // uniform mesh: [cstride] records Rec<R>; mapped: [NCOEF_M][cstride]
     unsigned char *flag;         // [cstride]
     double *F[3];                // face fluxes [10][nface_d]
     Ctl *ctl;                    // device control block
@@ -257,7 +257,8 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
     const size_t rsz = grid->precision == HGKS_MIXED ? sizeof(float) : sizeof(double);
     h->mesh = grid->mesh;
     const bool mapped = h->mesh != 0;
-    const int ncoef = mapped ? hk::NCOEF_M : hk::NCOEF;
+    const int ncoef = mapped ? hk::NCOEF_M
+                             : (grid->precision == HGKS_MIXED ? hk::Rec<float>::N : hk::Rec<double>::N);
     const int nfv = mapped ? hk::NFACE_M : 10;
     size_t sizes[] = {5 * g.pstride * sizeof(double), 5 * g.pstride * sizeof(double), 5 * g.ncell * sizeof(double),
                       ncoef * g.cstride * rsz, (size_t)g.cstride};
@@ -539,7 +540,7 @@ static int stage_fluxes(hgks_t *h, double *Q, int half = 0, bool geom_ready = fa
         float *c = (float *)h->coef;
         {
             PhaseTimer t(h, HGKS_PHASE_RECON, 3);
-            hk::launch_recon<float>(Q, c, h->flag, g, h->S, h->ctl, s, h->Qsplit);
+            hk::launch_recon<float>(Q, c, h->flag, g, h->S, h->ctl, s, (int *)h->F[2], h->Qsplit);
         }
         PhaseTimer t(h, HGKS_PHASE_FLUX, 3);
         for (int d = 0; d < 3; ++d) hk::launch_flux<float>(d, c, h->F[d], g, h->S, h->ctl, s);
@@ -547,7 +548,7 @@ static int stage_fluxes(hgks_t *h, double *Q, int half = 0, bool geom_ready = fa
         double *c = (double *)h->coef;
         {
             PhaseTimer t(h, HGKS_PHASE_RECON, 2);
-            hk::launch_recon<double>(Q, c, h->flag, g, h->S, h->ctl, s);
+            hk::launch_recon<double>(Q, c, h->flag, g, h->S, h->ctl, s, (int *)h->F[2]);
         }
         PhaseTimer t(h, HGKS_PHASE_FLUX, 3);
         for (int d = 0; d < 3; ++d) hk::launch_flux<double>(d, c, h->F[d], g, h->S, h->ctl, s);
@@ -682,12 +683,12 @@ extern "C" int hgks_reconstruct(hgks_t *h, double *coef, int *flag)
     if (h->mesh != 0) hk::launch_geom(h->geo, g, h->map, h->ctl, 0, 0.0, s);
     if (h->precision == HGKS_MIXED) {
         if (h->mesh != 0) hk::launch_recon_mapped<float>(h->Qn, h->geo, (float *)h->coef, h->flag, g, h->map, h->S, h->ctl, 0, s);
-        else hk::launch_recon<float>(h->Qn, (float *)h->coef, h->flag, g, h->S, h->ctl, s, h->Qsplit);
-        hk::launch_export_coef<float>((float *)h->coef, h->flag, g, dc, df, s);
+        else hk::launch_recon<float>(h->Qn, (float *)h->coef, h->flag, g, h->S, h->ctl, s, (int *)h->F[2], h->Qsplit);
+        hk::launch_export_coef<float>((float *)h->coef, h->flag, g, dc, df, s, h->mesh == 0);
     } else {
         if (h->mesh != 0) hk::launch_recon_mapped<double>(h->Qn, h->geo, (double *)h->coef, h->flag, g, h->map, h->S, h->ctl, 0, s);
-        else hk::launch_recon<double>(h->Qn, (double *)h->coef, h->flag, g, h->S, h->ctl, s);
-        hk::launch_export_coef<double>((double *)h->coef, h->flag, g, dc, df, s);
+        else hk::launch_recon<double>(h->Qn, (double *)h->coef, h->flag, g, h->S, h->ctl, s, (int *)h->F[2]);
+        hk::launch_export_coef<double>((double *)h->coef, h->flag, g, dc, df, s, h->mesh == 0);
     }
     hk::launch_set_ctl(h->ctl, h->ctl_host->t, 0.0, 0, s);
     // reconstruction, export and control reset; on a mapped mesh also the

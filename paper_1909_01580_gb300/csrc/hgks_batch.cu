@@ -7,6 +7,8 @@
 // retirement allocate nothing; a change of composition only rewrites the
 // device-side instance and tile tables that the captured kernels read.
 #include <cuda_runtime.h>
+
+#include <cmath>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -123,11 +125,23 @@ __global__ void __launch_bounds__(128) kb_recon(const BInst *__restrict__ I, con
         const BInst &in = I[T.inst];
         if (!in.ctl->active) continue;
         const double *Q = STAGE == 1 ? in.Qn : in.Qs;
+        // records staged in shared memory and stored coalesced, as in k_recon
+        extern __shared__ int4 kb_recon_stage_raw[];
+        R *stage = reinterpret_cast<R *>(kb_recon_stage_raw);
         for (long long b = T.first; b < T.last; b += blockDim.x) {
             const long long t = b + threadIdx.x;
-            if (t < T.last) hk::recon_item<R>(Q, (R *)in.coef, in.flag, in.g, in.S, in.ctl, t);
+            if (t < T.last) hk::recon_item<R>(Q, stage + threadIdx.x * hk::Rec<R>::N, in.flag, in.g, in.S, in.ctl, t);
+            hk::store_records<R>((R *)in.coef, stage, b, (int)std::min<long long>(blockDim.x, T.last - b));
         }
     }
+}
+
+// dynamic shared memory of kb_recon: one record per thread of the block
+template <typename R> static int recon_smem() { return BLOCK[TG_RECON] * hk::Rec<R>::N * (int)sizeof(R); }
+template <typename R> static void recon_smem_optin()
+{
+    cudaFuncSetAttribute(kb_recon<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, recon_smem<R>());
+    cudaFuncSetAttribute(kb_recon<R, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, recon_smem<R>());
 }
 
 template <typename R, int D>
@@ -273,7 +287,7 @@ static void inst_sizes(const Geo &g, int precision, size_t sz[8])
     sz[0] = align256(5 * (size_t)g.pstride * sizeof(double));
     sz[1] = sz[0];
     sz[2] = align256(5 * (size_t)g.ncell * sizeof(double));
-    sz[3] = align256(hk::NCOEF * (size_t)g.cstride * rsz);
+    sz[3] = align256((size_t)(rsz == sizeof(float) ? hk::Rec<float>::N : hk::Rec<double>::N) * g.cstride * rsz);
     sz[4] = align256((size_t)g.cstride);
     for (int d = 0; d < 3; ++d)
         sz[5 + d] = align256(10 * (size_t)(g.nx + (d == 0)) * (g.ny + (d == 1)) * (g.nz + (d == 2)) * sizeof(double));
@@ -416,13 +430,13 @@ template <typename R> static void launch_step_kernels(hgks_batch_t *b)
     kb_cfl<<<b->bps[TG_CFL] * n, BLOCK[TG_CFL], 0, s>>>(I, b->d_tiles[PH_CFL], nt);
     kb_dt<<<(b->nslot + 127) / 128, 128, 0, s>>>(I, b->d_inuse, b->nslot);
     kb_halo<1><<<b->bps[TG_HALO] * n, BLOCK[TG_HALO], 0, s>>>(I, b->d_tiles[PH_HALO], nt);
-    kb_recon<R, 1><<<b->bps[TG_RECON] * n, BLOCK[TG_RECON], 0, s>>>(I, b->d_tiles[PH_RECON], nt);
+    kb_recon<R, 1><<<b->bps[TG_RECON] * n, BLOCK[TG_RECON], recon_smem<R>(), s>>>(I, b->d_tiles[PH_RECON], nt);
     kb_flux<R, 0><<<b->bps[TG_FLUX] * n, BLOCK[TG_FLUX], 0, s>>>(I, b->d_tiles[PH_FX], nt);
     kb_flux<R, 1><<<b->bps[TG_FLUX] * n, BLOCK[TG_FLUX], 0, s>>>(I, b->d_tiles[PH_FY], nt);
     kb_flux<R, 2><<<b->bps[TG_FLUX] * n, BLOCK[TG_FLUX], 0, s>>>(I, b->d_tiles[PH_FZ], nt);
     kb_update<1><<<b->bps[TG_UPD] * n, BLOCK[TG_UPD], 0, s>>>(I, b->d_tiles[PH_UPD], nt);
     kb_halo<2><<<b->bps[TG_HALO] * n, BLOCK[TG_HALO], 0, s>>>(I, b->d_tiles[PH_HALO], nt);
-    kb_recon<R, 2><<<b->bps[TG_RECON] * n, BLOCK[TG_RECON], 0, s>>>(I, b->d_tiles[PH_RECON], nt);
+    kb_recon<R, 2><<<b->bps[TG_RECON] * n, BLOCK[TG_RECON], recon_smem<R>(), s>>>(I, b->d_tiles[PH_RECON], nt);
     kb_flux<R, 0><<<b->bps[TG_FLUX] * n, BLOCK[TG_FLUX], 0, s>>>(I, b->d_tiles[PH_FX], nt);
     kb_flux<R, 1><<<b->bps[TG_FLUX] * n, BLOCK[TG_FLUX], 0, s>>>(I, b->d_tiles[PH_FY], nt);
     kb_flux<R, 2><<<b->bps[TG_FLUX] * n, BLOCK[TG_FLUX], 0, s>>>(I, b->d_tiles[PH_FZ], nt);
@@ -477,6 +491,9 @@ extern "C" int hgks_batch_create(int precision, unsigned long long arena_bytes, 
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    // the reconstruction's record stage exceeds the default 48 KB in FP64
+    if (precision == HGKS_MIXED) recon_smem_optin<float>();
+    else recon_smem_optin<double>();
     if (stream) {
         b->stream = (cudaStream_t)stream;
     } else {
@@ -522,6 +539,22 @@ extern "C" int hgks_batch_create(int precision, unsigned long long arena_bytes, 
     return HGKS_OK;
 }
 
+// Admission check of a request's initial state (host FP64 [5][ncell]):
+// every value finite, density and pressure positive in every cell, so that
+// a bad request is refused before it takes a slot and never reaches the
+// graph that advances the others.
+static bool host_state_physical(const double *q, long long ncell, double gamma)
+{
+    for (long long c = 0; c < ncell; ++c) {
+        const double r = q[c], mx = q[ncell + c], my = q[2 * ncell + c], mz = q[3 * ncell + c], e = q[4 * ncell + c];
+        if (!std::isfinite(r) || !std::isfinite(mx) || !std::isfinite(my) || !std::isfinite(mz) || !std::isfinite(e))
+            return false;
+        const double p = (gamma - 1.0) * (e - 0.5 * (mx * mx + my * my + mz * mz) / r);
+        if (!(r > 0.0) || !(p > 0.0)) return false;
+    }
+    return true;
+}
+
 extern "C" int hgks_batch_add(hgks_batch_t *b, const hgks_grid_t *grid, double gamma, double mu, double Pr,
                               const int bc[6], const double *q, double t0, double t_end, double cfl, int *slot)
 {
@@ -529,6 +562,8 @@ extern "C" int hgks_batch_add(hgks_batch_t *b, const hgks_grid_t *grid, double g
     if (grid->precision != b->precision) return bfail(b, HGKS_E_INVALID, "instance precision differs from the batch");
     double hx;
     if (validate_grid(grid, gamma, mu, Pr, bc, &hx) != HGKS_OK) return bfail(b, HGKS_E_INVALID, "invalid instance");
+    if (!host_state_physical(q, (long long)grid->n[0] * grid->n[1] * grid->n[2], gamma))
+        return bfail(b, HGKS_E_NONPHYSICAL, "initial state not finite, or with non-positive density or pressure");
     int sl = -1;
     for (int i = 0; i < b->nslot && sl < 0; ++i)
         if (!b->inuse[i]) sl = i;
@@ -708,7 +743,7 @@ template <typename R> static void occupancy_caps(int cap[NTG])
     cap[TG_CFL] = std::max(1, v);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kb_halo<1>, BLOCK[TG_HALO], 0);
     cap[TG_HALO] = std::max(1, v);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kb_recon<R, 1>, BLOCK[TG_RECON], 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kb_recon<R, 1>, BLOCK[TG_RECON], recon_smem<R>());
     cap[TG_RECON] = std::max(1, v);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kb_flux<R, 0>, BLOCK[TG_FLUX], 0);
     cap[TG_FLUX] = std::max(1, v);

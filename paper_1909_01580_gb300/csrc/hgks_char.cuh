@@ -263,8 +263,7 @@ __device__ __forceinline__ void positivity_char_item(const double *__restrict__ 
             X[(d + 2) % 3] = gb ? R(GAUSS_S) : R(-GAUSS_S);
             R W[5];
             for (int v = 0; v < 5; ++v) W[v] = qcv[v] + poly9(cf[v], X);
-            const R p = (gamma - R(1)) * (W[4] - R(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / W[0]);
-            if (W[0] < R(0) || p < R(0)) bad = true;
+            if (W[0] < R(0) || pressure_negative(W)) bad = true;
         }
     }
     if (bad) {

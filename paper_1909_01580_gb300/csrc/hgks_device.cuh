@@ -111,13 +111,13 @@ template <> HK_HD FluxK<float> fluxk<float>(const Scheme &S) { return S.kf; }
 constexpr int GHOST = 3;
 struct Geo {
     int nx, ny, nz;          // interior cells
-    int px, py, pz;          // padded state extents (n + 4)
+    int px, py, pz;          // padded state extents (n + 2 GHOST)
     int cx, cy, cz;          // reconstruction extents (n + 2)
     long long pstride;       // px*py*pz: variable stride of padded state arrays
     long long cstride;       // cx*cy*cz: term stride of coefficient arrays
     long long ncell;         // nx*ny*nz
     double h, inv_h;         // cell edge and its inverse
-    int bc[6];               // 0 periodic, 1 reflective per face
+    int bc[6];               // per face: 0 periodic, 1 reflective, 2 outflow
 };
 
 HK_HD long long pidx(const Geo &g, int i, int j, int k)
@@ -142,9 +142,26 @@ HK_HD long long cidx(const Geo &g, int i, int j, int k)
 
 // Reconstruction storage per cell, in the working precision: for each of
 // the 5 variables the cell average Q_c (slot 0) and the 9 coefficients of
-// P~ - Q_c (slots 1..9); term stride Geo::cstride.
+// P~ - Q_c (slots 1..9).  The per-face arrays of the characteristic
+// variables and the mapped mesh's arrays keep one array per slot (term
+// stride = the number of faces or cells); the uniform mesh keeps one record
+// per cell (Rec below).
 constexpr int NCOEF = 50;
 HK_HD int coef_slot(int v, int n) { return v * 10 + n; }
+
+// One record per cell of the uniform mesh: variable v's 10 values at
+// v * VS .. v * VS + 9, every variable on a 16-byte boundary (FP32: 12
+// floats with 2 unused, loaded as 3 float4; FP64: 10 doubles, 5 double2),
+// so that the face flux reads a cell with a few vector loads at constant
+// offsets.
+template <typename R> struct Rec {
+    static constexpr int VS = sizeof(R) == 4 ? 12 : 10;
+    static constexpr int N = 5 * VS;
+};
+template <typename R> HK_HD long long rec_idx(long long cell, int v, int n)
+{
+    return cell * Rec<R>::N + v * Rec<R>::VS + n;
+}
 
 // Per-handle device control block: time, step and status.
 struct Ctl {
@@ -154,6 +171,7 @@ struct Ctl {
     int status;                  // bit 0: nonphysical state produced
     int steps_done;
     int flagged;                 // cells that took the positivity fallback (last stage)
+    unsigned nmarked;            // cells the reconstruction left to the literal positivity check
     double mapS, mapC;           // mapped mesh: sin(omega t), cos(omega t) at the stage time
                                  // (S = 1, C = 0 on a static mesh), set by the geometry kernel
     float mapAS, mapAUC;         // amp S and amp omega C in FP32 (mixed path)
@@ -753,6 +771,14 @@ template <typename R> HK_HD R bound_linear(const R b[3])
 {
     return R(0.5) * (m_abs(b[0]) + m_abs(b[1]) + m_abs(b[2]));
 }
+// the same for every linear P_m at once, at the cell's 24 face Gauss points
+// (where the positivity check looks), from the largest indicator
+// beta_m = |b|^2: |b . X| <= |b| |X| and every Gauss point has |X|^2 =
+// 1/4 + 2/12 = 5/12 (Cauchy-Schwarz)
+template <typename R> HK_HD R bound_linear_gauss(R beta_max)
+{
+    return m_sqrt(R(5.0 / 12.0) * beta_max);
+}
 template <typename R> HK_HD R bound_quadratic(const R a[9])
 {
     return R(0.5) * (m_abs(a[0]) + m_abs(a[1]) + m_abs(a[2]))
@@ -924,7 +950,7 @@ template <typename R> HK_HD void recip4(const R d[4], R x[4])
 // linear P_m, their indicators, tau of eq. (para), the nonlinear weights of
 // eq. (nonlinear) and P~ = (w0/g0) P0 + sum (w_m - w0 g_m/g0) P_m, returned
 // as the 9 coefficients of one quadratic; rad receives a rigorous bound of
-// |P_m(X) - Q_c| over the cell for all 25 polynomials.
+// |P_m(X) - Q_c| at the cell's 24 face Gauss points for all 25 polynomials.
 template <typename R>
 HK_HD void weno_ao(const Stencil<R> &st, const Scheme &S, R out[9], R &rad)
 {
@@ -932,7 +958,7 @@ HK_HD void weno_ao(const Stencil<R> &st, const Scheme &S, R out[9], R &rad)
     R a[9];
     big_stencil_P0(st, a);
     const R beta0 = beta_quadratic(a);
-    R r = bound_quadratic(a);
+    R bmax = R(0);
     AoSums<R> acc;
     acc.init(beta0, eps, S.weno_pow == 2);
 #define HK_PASS(M0, M1, M2, M3)                                                \
@@ -945,14 +971,14 @@ HK_HD void weno_ao(const Stencil<R> &st, const Scheme &S, R out[9], R &rad)
         for (int q = 0; q < 4; ++q) {                                          \
             bm[q] = b[q][0] * b[q][0] + b[q][1] * b[q][1] + b[q][2] * b[q][2]; \
             den[q] = bm[q] + eps;                                              \
-            r = m_max(r, bound_linear(b[q]));                                  \
+            bmax = m_max(bmax, bm[q]);                                         \
         }                                                                      \
         recip4(den, x);                                                        \
         for (int q = 0; q < 4; ++q) acc.add_x(beta0, b[q], bm[q], x[q]);      \
     }
     HK_FOR_SUBSTENCIL_QUADS(HK_PASS)
 #undef HK_PASS
-    rad = r;
+    rad = m_max(bound_quadratic(a), bound_linear_gauss(bmax));
     R iw, f0, lin[3];
     acc.template combine<24>(g0, gm, iw, f0, lin);
 #pragma unroll
@@ -969,7 +995,7 @@ HK_HD void weno_ao_sp(const Stencil<R> &st, const Scheme &S, R out[9], R &rad)
     R a[9];
     big_stencil_P0_sp(st, a);
     const R beta0 = beta_quadratic(a);
-    R r = bound_quadratic(a);
+    R bmax = R(0);
     AoSums<R> acc;
     acc.init(beta0, eps, S.weno_pow == 2);
 #define HK_PASS_SP(M0, M1, M2, M3)                                             \
@@ -982,22 +1008,35 @@ HK_HD void weno_ao_sp(const Stencil<R> &st, const Scheme &S, R out[9], R &rad)
         for (int q = 0; q < 4; ++q) {                                          \
             bm[q] = b[q][0] * b[q][0] + b[q][1] * b[q][1] + b[q][2] * b[q][2]; \
             den[q] = bm[q] + eps;                                              \
-            r = m_max(r, bound_linear(b[q]));                                  \
+            bmax = m_max(bmax, bm[q]);                                         \
         }                                                                      \
         recip4(den, x);                                                        \
         for (int q = 0; q < 4; ++q) acc.add_x(beta0, b[q], bm[q], x[q]);      \
     }
     HK_FOR_SUBSTENCIL_QUADS_SP(HK_PASS_SP)
 #undef HK_PASS_SP
-    rad = r;
+    rad = m_max(bound_quadratic(a), bound_linear_gauss(bmax));
     R iw, f0, lin[3];
     acc.template combine<8>(g0, gm, iw, f0, lin);
 #pragma unroll
     for (int n = 0; n < 9; ++n) out[n] = iw * (f0 * a[n] + (n < 3 ? lin[n] : R(0)));
 }
 
-// Sufficient test that no P_m gives negative density or pressure anywhere in
-// the cell, from the cell averages and the bounds rad[v]; when it fails the
+// The sign test of the pressure p = (gamma - 1)(rho E - |rho U|^2/(2 rho))
+// of a point state W, for rho >= 0 (a negative rho has failed already):
+// p < 0 exactly when 2 rho (rho E) - |rho U|^2 < 0, since gamma > 1; no
+// division.  (rho = 0 with rho U = 0 is not negative, as p is then NaN.)
+template <typename R> HK_HD bool pressure_negative(const R W[5])
+{
+    R q = R(2) * W[0] * W[4];
+    q -= W[1] * W[1];
+    q -= W[2] * W[2];
+    q -= W[3] * W[3];
+    return q < R(0);
+}
+
+// Sufficient test that no P_m gives negative density or pressure at the
+// cell's Gauss points, from the cell averages and the bounds rad[v]; when it fails the
 // literal check of the fallback (Sec. 4) decides.
 template <typename R> HK_HD bool positivity_certain(const R qc[5], const R rad[5], R gamma)
 {

@@ -14,7 +14,7 @@ namespace hk {
 
 // ---------------------------------------------------------------------------
 // ghost cells: periodic wrap, reflective mirror (normal momentum negated) or
-// non-reflecting outflow (the boundary cell repeated), width 2 including
+// non-reflecting outflow (the boundary cell repeated), GHOST layers including
 // edge and corner ghosts; every ghost reads its interior source directly, so
 // one pass fills all of them.  t: padded linear index.
 // ---------------------------------------------------------------------------
@@ -177,9 +177,9 @@ __device__ __noinline__ bool positivity_violated(const double *__restrict__ Q, c
             X[(d + 1) % 3] = ga ? R(GAUSS_S) : R(-GAUSS_S);
             X[(d + 2) % 3] = gb ? R(GAUSS_S) : R(-GAUSS_S);
             R W[5];
-            for (int v = 0; v < 5; ++v) W[v] = qcv[v] + poly9(cf[v], X);
-            const R p = (gamma - R(1)) * (W[4] - R(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / W[0]);
-            if (W[0] < R(0) || p < R(0)) return true;
+            for (int v = 0; v < 5; ++v)
+                W[v] = qcv[v] + (m == 0 ? poly9(cf[v], X) : cf[v][0] * X[0] + cf[v][1] * X[1] + cf[v][2] * X[2]);
+            if (W[0] < R(0) || pressure_negative(W)) return true;
         }
     }
     return false;
@@ -216,9 +216,9 @@ __device__ __noinline__ bool positivity_violated_sp(const double *__restrict__ Q
             X[(d + 1) % 3] = ga ? R(GAUSS_S) : R(-GAUSS_S);
             X[(d + 2) % 3] = gb ? R(GAUSS_S) : R(-GAUSS_S);
             R W[5];
-            for (int v = 0; v < 5; ++v) W[v] = qcv[v] + poly9(cf[v], X);
-            const R p = (gamma - R(1)) * (W[4] - R(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / W[0]);
-            if (W[0] < R(0) || p < R(0)) return true;
+            for (int v = 0; v < 5; ++v)
+                W[v] = qcv[v] + (m == 0 ? poly9(cf[v], X) : cf[v][0] * X[0] + cf[v][1] * X[1] + cf[v][2] * X[2]);
+            if (W[0] < R(0) || pressure_negative(W)) return true;
         }
     }
     return false;
@@ -232,10 +232,13 @@ __device__ __noinline__ bool positivity_violated_sp(const double *__restrict__ Q
 // the cells whose bound is inconclusive with flag 2
 // QS (mixed path): the differences come from the split state Qsplit,
 // [hi: 5][pstride] then [lo: 5][pstride]
+// rec: where cell t's record (Rec<R> layout) goes, a shared-memory stage
+// that store_records copies out
 template <typename R, bool SPLIT = false, bool QS = false>
-__device__ __forceinline__ void recon_item(const double *__restrict__ Q, R *__restrict__ coef,
+__device__ __forceinline__ void recon_item(const double *__restrict__ Q, R *__restrict__ rec,
                                            unsigned char *__restrict__ flag, const Geo &g, const Scheme &S, Ctl *ctl,
-                                           long long t, const float *__restrict__ Qsplit = nullptr)
+                                           long long t, const float *__restrict__ Qsplit = nullptr,
+                                           int *__restrict__ list = nullptr)
 {
     if (t >= g.cstride) return;
     int i, j, k;
@@ -263,14 +266,26 @@ __device__ __forceinline__ void recon_item(const double *__restrict__ Q, R *__re
         R out[9];
         if (S.sprime) weno_ao_sp(st, S, out, rad[v]);
         else weno_ao(st, S, out, rad[v]);
-        coef[coef_slot(v, 0) * g.cstride + t] = R(qc);
+        rec[v * Rec<R>::VS] = R(qc);
 #pragma unroll
-        for (int n = 0; n < 9; ++n) coef[coef_slot(v, 1 + n) * g.cstride + t] = out[n];
+        for (int n = 0; n < 9; ++n) rec[v * Rec<R>::VS + 1 + n] = out[n];
     }
     // positivity fallback: the cheap sufficient test first, the literal
     // check of all 25 polynomials at the 24 Gauss points only when it fails
     if (SPLIT) {
-        flag[t] = (S.limiter && !positivity_certain(qcv, rad, fluxk<R>(S).gamma)) ? 2 : 0;
+        // mark the cells the bound cannot certify and append them to the list
+        // of the literal check (one atomic per group of converged lanes)
+        const bool marked = S.limiter && !positivity_certain(qcv, rad, fluxk<R>(S).gamma);
+        flag[t] = marked ? 2 : 0;
+        const unsigned act = __activemask();
+        const unsigned m = __ballot_sync(act, marked);
+        if (m) {
+            const int lane = threadIdx.x & 31, leader = __ffs(act) - 1;
+            unsigned base = 0;
+            if (lane == leader) base = atomicAdd(&ctl->nmarked, (unsigned)__popc(m));
+            base = __shfl_sync(act, base, leader);
+            if (marked) list[base + __popc(m & ((1u << lane) - 1u))] = (int)t;
+        }
         return;
     }
     bool bad = false;
@@ -279,89 +294,199 @@ __device__ __forceinline__ void recon_item(const double *__restrict__ Q, R *__re
                        : positivity_violated<R>(Q, g, i, j, k, fluxk<R>(S).gamma);
     if (bad) {
         for (int v = 0; v < 5; ++v)
-            for (int n = 1; n < 10; ++n) coef[coef_slot(v, n) * g.cstride + t] = R(0);
+            for (int n = 1; n < 10; ++n) rec[v * Rec<R>::VS + n] = R(0);
         atomicAdd(&ctl->flagged, 1);
     }
     flag[t] = bad ? 1 : 0;
 }
 
-// the literal positivity check (Sec. 4) of the cells marked 2 by
-// recon_item<R, true>, one warp per cell: the warp takes its marked cells in
-// turn, lane m builds polynomial m (P0 for m = 0, the linear P_m after; 25
-// for S, 9 for S') from the cell's stencil and evaluates rho and p at the
-// cell's 24 face Gauss points, and a vote gives the verdict; a violation
-// sets P~ to the cell average.  Every lane of the warp must call this.
+// The records of a block's consecutive cells [b, b + n), staged in shared
+// memory (one record per thread, the global layout), copied out with 16-byte
+// stores: coalesced, where each thread storing its own record would touch a
+// sector per value.  Every thread of the block calls this after the stage
+// is written (it synchronises the block).
 template <typename R>
-__device__ __forceinline__ void positivity_item(const double *__restrict__ Q, R *__restrict__ coef,
+__device__ __forceinline__ void store_records(R *__restrict__ coef, const R *stage, long long b, int n)
+{
+    __syncthreads();
+    constexpr int PER = 16 / sizeof(R);
+    const int total = n * (Rec<R>::N / PER);
+    const int4 *src = reinterpret_cast<const int4 *>(stage);
+    int4 *dst = reinterpret_cast<int4 *>(coef + b * Rec<R>::N);
+    for (int e = threadIdx.x; e < total; e += blockDim.x) dst[e] = src[e];
+    __syncthreads();
+}
+
+// The literal positivity check (Sec. 4) of the cells marked 2 by
+// recon_item<R, true>: rho and p of every candidate polynomial (P0 and the
+// linear P_m: 24 for S, 8 for S') at every one of the cell's 24 face Gauss
+// points.  The marked cells are listed by the reconstruction (list[0 ..
+// ctl->nmarked)); one warp takes one listed cell at a time, the warps
+// striding over the list.  Per cell the warp stages the stencil
+// differences in shared memory once; lane m < nsub builds the linear P_m
+// and the warp checks them face by face, stopping at the first violation
+// anywhere in the warp (most marked cells at a discontinuity violate);
+// only a cell that passes them has P0 built (one lane per variable, into
+// shared memory) and checked, one Gauss point per lane.  A violation sets
+// P~ to the cell average.  Every polynomial's arithmetic is that of
+// sub_stencil / big_stencil_P0 on the same differences, and the same
+// (polynomial, point) pairs decide.
+template <typename R> struct PosStage {
+    R d[5][24];  // dQ per variable: f[dim][-/+] at 2 dim + s, e[plane][sa][sb] at 6 + 4 plane + 2 sa + sb,
+                 // the far axis cells of S' at 18 + 2 dim + s
+    R qc[5];
+    R a0[5][9];  // P0 of each variable
+};
+
+// value of X at a Gauss point: face-normal axis d at xd, then (d+1)%3 at xa, (d+2)%3 at xb
+template <typename R> __device__ __forceinline__ void gauss_point_frame(int d, R xd, R xa, R xb, R X[3])
+{
+    X[0] = d == 0 ? xd : (d == 1 ? xb : xa);
+    X[1] = d == 0 ? xa : (d == 1 ? xd : xb);
+    X[2] = d == 0 ? xb : (d == 1 ? xa : xd);
+}
+
+template <typename R>
+__device__ __forceinline__ void positivity_list(const double *__restrict__ Q, R *__restrict__ coef,
                                                 unsigned char *__restrict__ flag, const Geo &g, const Scheme &S,
-                                                Ctl *ctl, long long t)
+                                                Ctl *ctl, const int *__restrict__ list, PosStage<R> &sm,
+                                                long long warp, long long nwarps)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const bool mine = t < g.cstride && flag[t] == 2;
-    unsigned pending = __ballot_sync(FULL, mine);
-    const int npoly = S.sprime ? 9 : 25;
-    const R gamma = fluxk<R>(S).gamma;
-    while (pending) {
-        const int owner = __ffs(pending) - 1;
-        pending &= pending - 1;
-        const long long tc = __shfl_sync(FULL, t, owner);
+    const int nsub = S.sprime ? 8 : 24;
+    const int nslot = S.sprime ? 24 : 18;
+    const long long sx = 1, sy = g.px, sz = (long long)g.px * g.py;
+    const long long nmarked = ctl->nmarked;
+    for (long long e = warp; e < nmarked; e += nwarps) {
+        const long long t = list[e];
         int i, j, k;
-        split3(tc, g.cx, g.cy, i, j, k);
-        i -= 1;
-        j -= 1;
-        k -= 1;
-        bool bad = false;
-        if (lane < npoly) {
-            R cf[5][9], qcv[5];
-#pragma unroll 1
+        split3(t, g.cx, g.cy, i, j, k);
+        const long long c = pidx(g, i - 1, j - 1, k - 1);
+        // stage: lane L < nslot forms dQ of stencil slot L for the 5 variables
+        if (lane < nslot) {
+            long long off;
+            if (lane < 6) {
+                const int dd = lane >> 1;
+                const long long st = dd == 0 ? sx : (dd == 1 ? sy : sz);
+                off = (lane & 1) ? st : -st;
+            } else if (lane < 18) {
+                const int q = lane - 6, pl = q >> 2;
+                const long long sa = pl == 0 ? sx : (pl == 1 ? sy : sz);
+                const long long sb = pl == 0 ? sy : (pl == 1 ? sz : sx);
+                off = ((q & 2) ? sa : -sa) + ((q & 1) ? sb : -sb);
+            } else {
+                const int dd = (lane - 18) >> 1;
+                const long long st = dd == 0 ? sx : (dd == 1 ? sy : sz);
+                off = (lane & 1) ? 2 * st : -2 * st;
+            }
+#pragma unroll
             for (int v = 0; v < 5; ++v) {
                 const double *Qv = Q + v * g.pstride;
-                const double qc = Qv[pidx(g, i, j, k)];
-                qcv[v] = R(qc);
-                Stencil<R> st;
-                load_stencil(Qv, g, i, j, k, qc, st);
-                R c9[9];
-                if (lane == 0) {
-                    if (S.sprime) {
-                        load_stencil_far(Qv, g, i, j, k, qc, st);
-                        big_stencil_P0_sp(st, c9);
-                    } else {
-                        big_stencil_P0(st, c9);
-                    }
-                } else {
-                    R b[3];
-                    if (S.sprime) sub_stencil_sp_rt(st, lane - 1, b);
-                    else sub_stencil_rt(st, lane - 1, b);
-#pragma unroll
-                    for (int n = 0; n < 9; ++n) c9[n] = n < 3 ? b[n] : R(0);
-                }
-#pragma unroll
-                for (int n = 0; n < 9; ++n) cf[v][n] = c9[n];
+                sm.d[v][lane] = R(Qv[c + off] - Qv[c]);
             }
-#pragma unroll 1
-            for (int gq = 0; gq < 24; ++gq) {
-                const int d = gq / 8, side = (gq / 4) & 1, ga = (gq >> 1) & 1, gb = gq & 1;
-                R X[3];
-                X[d] = side ? R(0.5) : R(-0.5);
-                X[(d + 1) % 3] = ga ? R(GAUSS_S) : R(-GAUSS_S);
-                X[(d + 2) % 3] = gb ? R(GAUSS_S) : R(-GAUSS_S);
-                R W[5];
+        } else if (lane >= 24 && lane < 29) {
+            sm.qc[lane - 24] = R(Q[(lane - 24) * g.pstride + c]);
+        }
+        __syncwarp();
+        R qcv[5];
 #pragma unroll
-                for (int v = 0; v < 5; ++v) W[v] = qcv[v] + poly9(cf[v], X);
-                const R p = (gamma - R(1)) * (W[4] - R(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / W[0]);
-                if (W[0] < R(0) || p < R(0)) bad = true;
+        for (int v = 0; v < 5; ++v) qcv[v] = sm.qc[v];
+        // the linear P_m, m = lane
+        R b[5][3];
+        if (lane < nsub) {
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+                if (S.sprime) {
+                    const int sxp = (lane & 1) ? 0 : 1, syp = (lane & 2) ? 0 : 1, szp = (lane & 4) ? 0 : 1;
+                    b[v][0] = sxp ? sm.d[v][1] : -sm.d[v][0];
+                    b[v][1] = syp ? sm.d[v][3] : -sm.d[v][2];
+                    b[v][2] = szp ? sm.d[v][5] : -sm.d[v][4];
+                } else {
+                    const int pl = lane >> 3, sg = lane & 7;
+                    const int sa = (sg & 1) ? 0 : 1, sb = (sg & 2) ? 0 : 1, sc = (sg & 4) ? 0 : 1;
+                    const int a = pl, bb = (pl + 1) % 3, cc = (pl + 2) % 3;
+                    const R qa = sm.d[v][2 * a + sa], qb = sm.d[v][2 * bb + sb];
+                    const R qab = sm.d[v][6 + 4 * pl + 2 * sa + sb], qcc = sm.d[v][2 * cc + sc];
+                    const R ba = (R(2) * qa - qb + qab) * R(1.0 / 3.0);
+                    const R bbv = (R(2) * qb - qa + qab) * R(1.0 / 3.0);
+                    const R va = sa ? ba : -ba, vb = sb ? bbv : -bbv, vc = sc ? qcc : -qcc;
+                    b[v][0] = a == 0 ? va : (bb == 0 ? vb : vc);
+                    b[v][1] = a == 1 ? va : (bb == 1 ? vb : vc);
+                    b[v][2] = a == 2 ? va : (bb == 2 ? vb : vc);
+                }
             }
         }
-        bad = __any_sync(FULL, bad);
-        if (lane == owner) {
+        bool bad = false;
+#pragma unroll 1
+        for (int fc = 0; fc < 6; ++fc) {
+            if (lane < nsub) {
+#pragma unroll
+                for (int gp = 0; gp < 4; ++gp) {
+                    R X[3];
+                    gauss_point_frame<R>(fc >> 1, (fc & 1) ? R(0.5) : R(-0.5), (gp & 2) ? R(GAUSS_S) : R(-GAUSS_S),
+                                         (gp & 1) ? R(GAUSS_S) : R(-GAUSS_S), X);
+                    R W[5];
+#pragma unroll
+                    for (int v = 0; v < 5; ++v)
+                        W[v] = qcv[v] + (b[v][0] * X[0] + b[v][1] * X[1] + b[v][2] * X[2]);
+                    if (W[0] < R(0) || pressure_negative(W)) bad = true;
+                }
+            }
+            if (__any_sync(FULL, bad)) {
+                bad = true;
+                break;
+            }
+        }
+        if (!bad) {
+            // P0: lane v < 5 builds variable v, then lane gq < 24 checks Gauss point gq
+            if (lane < 5) {
+                Stencil<R> st;
+#pragma unroll
+                for (int dd = 0; dd < 3; ++dd) {
+                    st.f[dd][0] = sm.d[lane][2 * dd];
+                    st.f[dd][1] = sm.d[lane][2 * dd + 1];
+                    st.f2[dd][0] = S.sprime ? sm.d[lane][18 + 2 * dd] : R(0);
+                    st.f2[dd][1] = S.sprime ? sm.d[lane][19 + 2 * dd] : R(0);
+                }
+#pragma unroll
+                for (int pl = 0; pl < 3; ++pl)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) st.e[pl][q >> 1][q & 1] = sm.d[lane][6 + 4 * pl + q];
+                R a[9];
+                if (S.sprime) big_stencil_P0_sp(st, a);
+                else big_stencil_P0(st, a);
+#pragma unroll
+                for (int n = 0; n < 9; ++n) sm.a0[lane][n] = a[n];
+            }
+            __syncwarp();
+            if (lane < 24) {
+                const int gq = lane;
+                R X[3];
+                gauss_point_frame<R>(gq / 8, ((gq / 4) & 1) ? R(0.5) : R(-0.5),
+                                     ((gq >> 1) & 1) ? R(GAUSS_S) : R(-GAUSS_S), (gq & 1) ? R(GAUSS_S) : R(-GAUSS_S),
+                                     X);
+                R W[5];
+#pragma unroll
+                for (int v = 0; v < 5; ++v) {
+                    R a[9];
+#pragma unroll
+                    for (int n = 0; n < 9; ++n) a[n] = sm.a0[v][n];
+                    W[v] = qcv[v] + poly9(a, X);
+                }
+                if (W[0] < R(0) || pressure_negative(W)) bad = true;
+            }
+            bad = __any_sync(FULL, bad);
+        }
+        if (lane == 0) {
             if (bad) {
                 for (int v = 0; v < 5; ++v)
-                    for (int n = 1; n < 10; ++n) coef[coef_slot(v, n) * g.cstride + t] = R(0);
+                    for (int n = 1; n < 10; ++n) coef[rec_idx<R>(t, v, n)] = R(0);
                 atomicAdd(&ctl->flagged, 1);
             }
             flag[t] = bad ? 1 : 0;
         }
+        __syncwarp();  // the stage is rewritten for the next cell
     }
 }
 
@@ -373,7 +498,28 @@ __device__ __forceinline__ void positivity_item(const double *__restrict__ Q, R 
 // per unit area, F and dF/dt, in FP64.  t: 4 * face + Gauss point; t beyond
 // the faces computes a clamped face and writes nothing.
 // ---------------------------------------------------------------------------
-template <typename R, int D>
+// the 10 values of variable v of a uniform-mesh record (Rec<R>) by vector loads
+__device__ __forceinline__ void load_rec_var(const float *__restrict__ rec, int v, float &q0, float c[9])
+{
+    const float4 *p = reinterpret_cast<const float4 *>(rec + v * Rec<float>::VS);
+    const float4 a = __ldg(p), b = __ldg(p + 1), d = __ldg(p + 2);
+    q0 = a.x;
+    c[0] = a.y; c[1] = a.z; c[2] = a.w;
+    c[3] = b.x; c[4] = b.y; c[5] = b.z; c[6] = b.w;
+    c[7] = d.x; c[8] = d.y;
+}
+__device__ __forceinline__ void load_rec_var(const double *__restrict__ rec, int v, double &q0, double c[9])
+{
+    const double2 *p = reinterpret_cast<const double2 *>(rec + v * Rec<double>::VS);
+    const double2 a = __ldg(p), b = __ldg(p + 1), d = __ldg(p + 2), e = __ldg(p + 3), f = __ldg(p + 4);
+    q0 = a.x;
+    c[0] = a.y; c[1] = b.x; c[2] = b.y; c[3] = d.x; c[4] = d.y;
+    c[5] = e.x; c[6] = e.y; c[7] = f.x; c[8] = f.y;
+}
+
+// REC: coef is the cell's record (Rec<R>); otherwise one array per slot
+// with term stride `stride` and the cell at ci
+template <typename R, int D, bool REC = false>
 __device__ __forceinline__ void eval_side(const R *__restrict__ coef, long long stride, long long ci, R xd, R xa,
                                           R xb, R W[5], R dW[3][5])
 {
@@ -391,10 +537,14 @@ __device__ __forceinline__ void eval_side(const R *__restrict__ coef, long long 
     R val[5], grad[5][3];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-        R c[9];
+        R c[9], e;
+        if constexpr (REC) {
+            load_rec_var(coef, v, e, c);
+        } else {
 #pragma unroll
-        for (int n = 0; n < 9; ++n) c[n] = coef[coef_slot(v, 1 + n) * stride + ci];
-        R e = coef[coef_slot(v, 0) * stride + ci];
+            for (int n = 0; n < 9; ++n) c[n] = coef[coef_slot(v, 1 + n) * stride + ci];
+            e = coef[coef_slot(v, 0) * stride + ci];
+        }
         e += c[D] * xd;
         e += c[3 + D] * R(1.0 / 6.0);
         e += xa * (c[A] + c[DA] * xd);
@@ -460,8 +610,8 @@ __device__ __forceinline__ void flux_item(const R *__restrict__ coef, double *__
         eval_side<R, D>(coef, nface, face, R(0.5), xa, xb, Wl, dWl);
         eval_side<R, D>(coef + 50 * nface, nface, face, R(-0.5), xa, xb, Wr, dWr);
     } else {
-        eval_side<R, D>(coef, g.cstride, cidx(g, il, jl, kl), R(0.5), xa, xb, Wl, dWl);
-        eval_side<R, D>(coef, g.cstride, cidx(g, i, j, k), R(-0.5), xa, xb, Wr, dWr);
+        eval_side<R, D, true>(coef + cidx(g, il, jl, kl) * Rec<R>::N, 0, 0, R(0.5), xa, xb, Wl, dWl);
+        eval_side<R, D, true>(coef + cidx(g, i, j, k) * Rec<R>::N, 0, 0, R(-0.5), xa, xb, Wr, dWr);
     }
     R F[5], dF[5];
     gks_flux<R>(Wl, dWl, Wr, dWr, S, R(dt), F, dF, R(g.inv_h));

@@ -1,6 +1,8 @@
 // Kernels of the HGKS stage sweep on sm_103a (uniform mesh of cubes):
 // ghost fill, WENO-AO reconstruction (Sec. 2), Gauss-point gas-kinetic
 // face flux (Sec. 3), two-stage update and CFL reduction.
+#include <algorithm>
+
 #include "hgks_kernels.cuh"
 #include "hgks_items.cuh"
 
@@ -11,13 +13,20 @@ __global__ void k_halo(double *__restrict__ Q, Geo g)
     halo_item(Q, g, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
+// one thread per cell of the reconstruction box; the block's records are
+// staged in dynamic shared memory (blockDim x Rec<R>::N values) and stored
+// coalesced
 template <typename R, bool QS>
 __global__ void __launch_bounds__(128) k_recon(const double *__restrict__ Q, R *__restrict__ coef,
                                                unsigned char *__restrict__ flag, Geo g, Scheme S, Ctl *ctl,
-                                               const float *__restrict__ Qsplit)
+                                               const float *__restrict__ Qsplit, int *__restrict__ list)
 {
     if (!ctl->active) return;
-    recon_item<R, true, QS>(Q, coef, flag, g, S, ctl, (long long)blockIdx.x * blockDim.x + threadIdx.x, Qsplit);
+    extern __shared__ int4 recon_stage_raw[];
+    R *stage = reinterpret_cast<R *>(recon_stage_raw);
+    const long long b = (long long)blockIdx.x * blockDim.x;
+    recon_item<R, true, QS>(Q, stage + threadIdx.x * Rec<R>::N, flag, g, S, ctl, b + threadIdx.x, Qsplit, list);
+    store_records<R>(coef, stage, b, (int)std::min<long long>(blockDim.x, g.cstride - b));
 }
 
 __global__ void k_split(const double *__restrict__ Q, float *__restrict__ hi, float *__restrict__ lo, long long n)
@@ -25,12 +34,18 @@ __global__ void k_split(const double *__restrict__ Q, float *__restrict__ hi, fl
     split_item(Q, hi, lo, n, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
+// the literal positivity check of the listed cells: persistent warps that
+// stride over the list, one cell per warp at a time
 template <typename R>
 __global__ void __launch_bounds__(128) k_positivity(const double *__restrict__ Q, R *__restrict__ coef,
-                                                    unsigned char *__restrict__ flag, Geo g, Scheme S, Ctl *ctl)
+                                                    unsigned char *__restrict__ flag, Geo g, Scheme S, Ctl *ctl,
+                                                    const int *__restrict__ list)
 {
     if (!ctl->active) return;
-    positivity_item<R>(Q, coef, flag, g, S, ctl, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    __shared__ PosStage<R> stage[4];
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    positivity_list<R>(Q, coef, flag, g, S, ctl, list, stage[threadIdx.x >> 5], warp, nwarps);
 }
 
 // resident blocks of 128 threads per SM asked of the compiler for the face
@@ -130,9 +145,10 @@ __global__ void k_gather(const double *__restrict__ Q, double *__restrict__ dst,
 }
 
 // coefficients of the interior cells to FP64 [ncell][5][9]
+// (rec: the uniform mesh's per-cell records; otherwise one array per slot)
 template <typename R>
 __global__ void k_export_coef(const R *__restrict__ coef, const unsigned char *__restrict__ flag, Geo g,
-                              double *__restrict__ out, int *__restrict__ oflag)
+                              double *__restrict__ out, int *__restrict__ oflag, bool rec)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.ncell) return;
@@ -140,7 +156,9 @@ __global__ void k_export_coef(const R *__restrict__ coef, const unsigned char *_
     split3(t, g.nx, g.ny, i, j, k);
     const long long ci = cidx(g, i, j, k);
     for (int v = 0; v < 5; ++v)
-        for (int n = 0; n < 9; ++n) out[t * 45 + v * 9 + n] = double(coef[coef_slot(v, 1 + n) * g.cstride + ci]);
+        for (int n = 0; n < 9; ++n)
+            out[t * 45 + v * 9 + n] =
+                double(rec ? coef[rec_idx<R>(ci, v, 1 + n)] : coef[coef_slot(v, 1 + n) * g.cstride + ci]);
     if (oflag) oflag[t] = flag[ci];
 }
 
@@ -195,6 +213,20 @@ __global__ void k_point_flux(int n, const double *__restrict__ in, const double 
 // ---------------------------------------------------------------------------
 static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// multiprocessors of the current device (cached per device)
+static int sm_count()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (cache[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
 void launch_halo(double *Q, const Geo &g, cudaStream_t s)
 {
     k_halo<<<blocks_for(g.pstride, 256), 256, 0, s>>>(Q, g);
@@ -202,15 +234,27 @@ void launch_halo(double *Q, const Geo &g, cudaStream_t s)
 
 template <typename R>
 void launch_recon(const double *Q, R *coef, unsigned char *flag, const Geo &g, const Scheme &S, Ctl *ctl,
-                  cudaStream_t s, float *split)
+                  cudaStream_t s, int *list, float *split)
 {
+    cudaMemsetAsync(&ctl->nmarked, 0, sizeof(unsigned), s);
     if (split) {
         const long long n = 5 * g.pstride;
         k_split<<<blocks_for(n, 256), 256, 0, s>>>(Q, split, split + n, n);
     }
-    if (split) k_recon<R, true><<<blocks_for(g.cstride, 128), 128, 0, s>>>(Q, coef, flag, g, S, ctl, split);
-    else k_recon<R, false><<<blocks_for(g.cstride, 128), 128, 0, s>>>(Q, coef, flag, g, S, ctl, nullptr);
-    k_positivity<R><<<blocks_for(g.cstride, 128), 128, 0, s>>>(Q, coef, flag, g, S, ctl);
+    const int smem = 128 * Rec<R>::N * (int)sizeof(R);  // 30 KB FP32, 50 KB FP64 (opted in at first use)
+    // the attribute is per device: set once per device and kernel
+    static bool opted[64][2] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !opted[dev][split ? 1 : 0]) {
+        if (split) cudaFuncSetAttribute(k_recon<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        else cudaFuncSetAttribute(k_recon<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (dev >= 0 && dev < 64) opted[dev][split ? 1 : 0] = true;
+    }
+    if (split) k_recon<R, true><<<blocks_for(g.cstride, 128), 128, smem, s>>>(Q, coef, flag, g, S, ctl, split, list);
+    else k_recon<R, false><<<blocks_for(g.cstride, 128), 128, smem, s>>>(Q, coef, flag, g, S, ctl, nullptr, list);
+    // persistent: 8 blocks of 4 warps per SM stride over the list of marked cells
+    k_positivity<R><<<8u * (unsigned)sm_count(), 128, 0, s>>>(Q, coef, flag, g, S, ctl, list);
 }
 
 template <typename R>
@@ -266,9 +310,9 @@ void launch_gather(const double *Q, double *dst, const Geo &g, cudaStream_t s)
 
 template <typename R>
 void launch_export_coef(const R *coef, const unsigned char *flag, const Geo &g, double *out, int *oflag,
-                        cudaStream_t s)
+                        cudaStream_t s, bool rec)
 {
-    k_export_coef<R><<<blocks_for(g.ncell, 128), 128, 0, s>>>(coef, flag, g, out, oflag);
+    k_export_coef<R><<<blocks_for(g.ncell, 128), 128, 0, s>>>(coef, flag, g, out, oflag, rec);
 }
 
 template <typename R>
@@ -279,15 +323,15 @@ void launch_point_flux(int n, const double *in, const double *ug, double dt, con
 }
 
 template void launch_recon<double>(const double *, double *, unsigned char *, const Geo &, const Scheme &, Ctl *,
-                                   cudaStream_t, float *);
+                                   cudaStream_t, int *, float *);
 template void launch_recon<float>(const double *, float *, unsigned char *, const Geo &, const Scheme &, Ctl *,
-                                  cudaStream_t, float *);
+                                  cudaStream_t, int *, float *);
 template void launch_flux<double>(int, const double *, double *, const Geo &, const Scheme &, Ctl *, cudaStream_t);
 template void launch_flux<float>(int, const float *, double *, const Geo &, const Scheme &, Ctl *, cudaStream_t);
 template void launch_export_coef<double>(const double *, const unsigned char *, const Geo &, double *, int *,
-                                         cudaStream_t);
+                                         cudaStream_t, bool);
 template void launch_export_coef<float>(const float *, const unsigned char *, const Geo &, double *, int *,
-                                        cudaStream_t);
+                                        cudaStream_t, bool);
 template void launch_point_flux<double>(int, const double *, const double *, double, const Scheme &, double *,
                                         double *, cudaStream_t);
 template void launch_point_flux<float>(int, const double *, const double *, double, const Scheme &, double *,

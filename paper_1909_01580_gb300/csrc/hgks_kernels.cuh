@@ -9,8 +9,11 @@ void launch_halo(double *Q, const Geo &g, cudaStream_t s);
 // split state of Q is formed first (one more launch) and the FP32
 // reconstruction takes its differences from it
 template <typename R>
+// list: room for one int per cell of the (n+2)^3 box, free until the
+// reconstruction's positivity pass ends (the callers lend the z-face flux
+// buffer, which the z sweep of the same stage overwrites afterwards)
 void launch_recon(const double *Q, R *coef, unsigned char *flag, const Geo &g, const Scheme &S, Ctl *ctl,
-                  cudaStream_t s, float *split = nullptr);
+                  cudaStream_t s, int *list, float *split = nullptr);
 template <typename R>
 void launch_flux(int axis, const R *coef, double *F, const Geo &g, const Scheme &S, Ctl *ctl, cudaStream_t s);
 void launch_update(int stage, double *Qn, double *Qs, double *Wacc, const double *Fx, const double *Fy,
@@ -26,7 +29,7 @@ void launch_scatter(const double *src, double *Q, const Geo &g, cudaStream_t s);
 void launch_gather(const double *Q, double *dst, const Geo &g, cudaStream_t s);
 template <typename R>
 void launch_export_coef(const R *coef, const unsigned char *flag, const Geo &g, double *out, int *oflag,
-                        cudaStream_t s);
+                        cudaStream_t s, bool rec);
 template <typename R>
 void launch_point_flux(int n, const double *in, const double *ug, double dt, const Scheme &S, double *F, double *dF,
                        cudaStream_t s);

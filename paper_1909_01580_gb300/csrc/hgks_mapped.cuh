@@ -518,8 +518,7 @@ __device__ __forceinline__ bool positivity_violated_mapped(const double *__restr
             const R X[3] = {R(Xd[0]), R(Xd[1]), R(Xd[2])};
             R W[5];
             for (int v = 0; v < 5; ++v) W[v] = qcv[v] + poly9_mapped(cf[v], X, Mh);
-            const R p = (gamma - R(1)) * (W[4] - R(0.5) * (W[1] * W[1] + W[2] * W[2] + W[3] * W[3]) / W[0]);
-            if (W[0] < R(0) || p < R(0)) return true;
+            if (W[0] < R(0) || pressure_negative(W)) return true;
         }
     }
     return false;

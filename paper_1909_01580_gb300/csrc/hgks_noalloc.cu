@@ -142,7 +142,7 @@ extern "C" int hgks_flux_noalloc(const hgks_grid_t *grid, double gamma, double m
     size_t off_ctl = 0;
     size_t off_q = off_ctl + round256(sizeof(Ctl));
     size_t off_coef = off_q + round256(5 * (size_t)g.pstride * sizeof(double));
-    size_t off_flag = off_coef + round256(hk::NCOEF * (size_t)g.cstride * rsz);
+    size_t off_flag = off_coef + round256((size_t)(mixed ? hk::Rec<float>::N : hk::Rec<double>::N) * g.cstride * rsz);
     size_t off_f[3];
     size_t end = off_flag + round256((size_t)g.cstride);
     for (int d = 0; d < 3; ++d) {
@@ -177,17 +177,20 @@ extern "C" int hgks_flux_noalloc(const hgks_grid_t *grid, double gamma, double m
     // control block (time, dt, counters) by k_set_ctl, the interior state by
     // the scatter, every ghost cell by the halo, every coefficient and flag
     // of the reconstruction box by the reconstruction, every face flux by
-    // the flux kernels, and (mixed) the split state by the split kernel before
-    // the reconstruction reads it.  Nothing of an earlier call is read.
+    // the flux kernels, (mixed) the split state by the split kernel before
+    // the reconstruction reads it, and the list of cells left to the literal
+    // positivity check (kept in the z-face flux area until the z sweep) and
+    // its count by the reconstruction after a reset.  Nothing of an earlier
+    // call is read.
     hk::launch_init_ctl(ctl, 0.0, s);
     hk::launch_set_ctl(ctl, 0.0, dt, 1, s);
     hk::launch_scatter(q, Q, g, s);
     hk::launch_halo(Q, g, s);
     if (mixed) {
-        hk::launch_recon<float>(Q, (float *)coef, flag, g, S, ctl, s, split);
+        hk::launch_recon<float>(Q, (float *)coef, flag, g, S, ctl, s, (int *)F[2], split);
         for (int d = 0; d < 3; ++d) hk::launch_flux<float>(d, (const float *)coef, F[d], g, S, ctl, s);
     } else {
-        hk::launch_recon<double>(Q, (double *)coef, flag, g, S, ctl, s);
+        hk::launch_recon<double>(Q, (double *)coef, flag, g, S, ctl, s, (int *)F[2]);
         for (int d = 0; d < 3; ++d) hk::launch_flux<double>(d, (const double *)coef, F[d], g, S, ctl, s);
     }
     hk::launch_residual(F[0], F[1], F[2], g, L, dLdt, s);

@@ -187,6 +187,7 @@ def serve_batched(reqs, precision=hgks.HGKS_FP64, arena_bytes=4 << 30, max_insta
     t_start = time.perf_counter()
     last_steps = {}
     waiting = []
+    rejected = {}
     while pending or waiting or by_slot:
         now = time.perf_counter() - t_start
         while pending and pending[0].arrival <= now:
@@ -205,6 +206,12 @@ def serve_batched(reqs, precision=hgks.HGKS_FP64, arena_bytes=4 << 30, max_insta
                     if not by_slot:
                         raise RuntimeError(f"request {r.rid} ({r.n}^3) does not fit the arena alone") from e
                     break  # wait for memory or a slot
+                if e.code == hgks.HGKS_E_NONPHYSICAL:
+                    # refused at admission (non-finite or non-positive state):
+                    # reported, and the resident requests go on untouched
+                    rejected[r.rid] = str(e)
+                    waiting.pop(k)
+                    continue
                 raise
             by_slot[sl] = r
             admitted_at[r.rid] = now
@@ -233,7 +240,7 @@ def serve_batched(reqs, precision=hgks.HGKS_FP64, arena_bytes=4 << 30, max_insta
     launches = b.launches
     b.close()
     return {"latency": lat, "makespan": makespan, "results": results, "cell_stages": cell_stages,
-            "launches": launches, "max_resident": max_resident}
+            "launches": launches, "max_resident": max_resident, "rejected": rejected}
 
 
 def summary(name, out, reqs):

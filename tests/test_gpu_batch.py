@@ -7,7 +7,7 @@ import pytest
 
 from paper_1909_01580_gb300 import hgks, serving
 from paper_1909_01580_gb300 import workloads as W
-from tests._cases import max_rel
+from tests._cases import max_rel, max_rel_momentum
 
 pytestmark = pytest.mark.gpu
 
@@ -132,3 +132,47 @@ def test_serving_results_same_alone_and_in_the_mix():
         assert max_rel(out["results"][r.rid], qa) <= 1e-11
     fifo = serving.serve_fifo(reqs)
     assert set(fifo["latency"]) == {r.rid for r in reqs}
+
+
+@pytest.mark.parametrize("precision,tol", [(hgks.HGKS_FP64, 1e-11), (hgks.HGKS_MIXED, 1e-4)])
+def test_batch_instances_against_the_oracle(precision, tol):
+    """Every instance of a batch (staggered ends, reflective and periodic
+    boxes) against the FP64 oracle run with the same CFL steps to the same
+    end time: FP64 per variable <= 1e-11, mixed <= 1e-4 (the FP32
+    reconstruction and flux; the momenta against the momentum scale, since
+    rho W of the Taylor-Green vortex starts at zero)."""
+    import oracle
+    hgks.load()
+    cases = _cases()[:3]
+    ends = [0.05, 0.02, 0.03]
+    b = hgks.Batch(precision, arena_bytes=256 << 20, max_instances=4)
+    slots = [b.add(n, lo, hi, q, t0=0.0, t_end=te, **kw) for (n, lo, hi, q, kw), te in zip(cases, ends)]
+    while True:
+        b.step(2)
+        t, steps, state = b.poll()
+        if all(state[sl] == 2 for sl in slots):
+            break
+        assert not any(state[sl] == 3 for sl in slots)
+    for sl, (n, lo, hi, q, kw), te in zip(slots, cases, ends):
+        cfg = oracle.make_cfg(n, lo, hi, **kw)
+        qo, to, done_o, _ = oracle.step(cfg, q, 0.0, 100000, cfl=0.35, t_end=te)
+        assert abs(t[sl] - to) < 1e-13 and steps[sl] == done_o, (t[sl], to, steps[sl], done_o)
+        qb = b.get_state(sl)
+        err = max_rel(qb, qo) if precision == hgks.HGKS_FP64 else max_rel_momentum(qb, qo)
+        assert err <= tol, (sl, err)
+    b.close()
+
+
+def test_served_requests_against_the_oracle():
+    """Requests served by continuous batching (FP64) against the oracle's
+    run of the same request to its end time, per variable <= 1e-11."""
+    import oracle
+    hgks.load()
+    reqs = serving.request_stream(count=3, seed=9, sizes=(8, 12), steps=(4, 10))
+    serving.poisson_arrivals(reqs, rate=500.0, seed=9)
+    out = serving.serve_batched(reqs, precision=hgks.HGKS_FP64, arena_bytes=128 << 20, max_instances=4,
+                                steps_per_poll=2)
+    for r in reqs:
+        cfg = oracle.make_cfg((r.n,) * 3, r.lo, r.hi, mu=r.mu, Pr=r.Pr)
+        qo, to, _, _ = oracle.step(cfg, r.q0, 0.0, 100000, cfl=0.35, t_end=r.t_end)
+        assert max_rel(out["results"][r.rid], qo) <= 1e-11, (r.rid, max_rel(out["results"][r.rid], qo))
