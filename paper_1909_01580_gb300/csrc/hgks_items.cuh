@@ -582,6 +582,16 @@ __device__ __forceinline__ void eval_side(const R *__restrict__ coef, long long 
     }
 }
 
+// resident blocks of 128 threads per SM asked of the compiler for the
+// single-instance face flux kernel.  FP64: no hint (238 registers, 2
+// blocks; 3 blocks with 168 registers and spills measured slower).  FP32: 5
+// blocks (96 registers, 56 bytes spilled), measured on the TGV 128^3 step
+// at 3.02 ms of flux against 3.20 ms at 4 blocks (128 registers), 3.23 ms
+// at 6 and 3.60 ms at 3.  (The batched flux kernel, with its tile loop,
+// spills more at 96 registers and runs faster without the hint.)
+template <typename R> struct FluxOcc { static constexpr int blocks = 1; };
+template <> struct FluxOcc<float> { static constexpr int blocks = 5; };
+
 template <int D> __device__ __forceinline__ long long face_count(const Geo &g)
 {
     return (long long)(g.nx + (D == 0)) * (g.ny + (D == 1)) * (g.nz + (D == 2));

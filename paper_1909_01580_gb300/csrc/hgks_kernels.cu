@@ -48,12 +48,6 @@ __global__ void __launch_bounds__(128) k_positivity(const double *__restrict__ Q
     positivity_list<R>(Q, coef, flag, g, S, ctl, list, stage[threadIdx.x >> 5], warp, nwarps);
 }
 
-// resident blocks of 128 threads per SM asked of the compiler for the face
-// flux kernel.  The FP32 kernel runs at 4 (127 registers, no spills): 3%
-// faster on GB300 than at 5 (96 registers with spills).
-template <typename R> struct FluxOcc { static constexpr int blocks = 1; };
-template <> struct FluxOcc<float> { static constexpr int blocks = 4; };
-
 template <typename R, int D>
 __global__ void __launch_bounds__(128, FluxOcc<R>::blocks) k_face_flux(const R *__restrict__ coef, double *__restrict__ Fout, Geo g,
                                                    Scheme S, Ctl *ctl)
