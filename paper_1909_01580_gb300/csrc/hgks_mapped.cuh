@@ -782,12 +782,24 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
     }
 
     // P0 of every variable with the big stencil's normal matrix, factored
-    // once; beta0 and the coefficients are parked in the output slots (0 and
-    // 1..9 of each variable) until the weights are known
+    // once.  FP32: P0 and beta0 stay in registers until the weights are
+    // known; FP64 (more registers per value) parks them in the output slots
+    // (0 and 1..9 of each variable)
+    constexpr bool fold = RmStage<R>::dq;
+    R p0[5][9], beta0[5];
     {
         R N[45];
 #pragma unroll
         for (int e = 0; e < 45; ++e) N[e] = R(0);
+        // FP32: the five right-hand sides A^T dQ gathered in the same sweep
+        // over the 18 rows as the normal matrix (each row, and the
+        // neighbour's second moments it reads, formed once); FP64 sweeps
+        // again per variable below
+        R rhs[5][9];
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+#pragma unroll
+            for (int n = 0; n < 9; ++n) rhs[v][n] = R(0);
 #pragma unroll 1
         for (int s = 0; s < 18; ++s) {
             int o[3];
@@ -798,24 +810,7 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
             for (int a = 0; a < 9; ++a)
 #pragma unroll
                 for (int b = 0; b <= a; ++b) N[a * (a + 1) / 2 + b] += row[a] * row[b];
-        }
-        chol_factor<R, 9>(N);
-        // (221 registers against 152 without: 7% faster on GB300 all the same)
-        constexpr bool fold = RmStage<R>::dq;
-        if constexpr (fold) {
-            // FP32: the five right-hand sides A^T dQ in one sweep over the
-            // staged rows and differences
-            R rhs[5][9];
-#pragma unroll
-            for (int v = 0; v < 5; ++v)
-#pragma unroll
-                for (int n = 0; n < 9; ++n) rhs[v][n] = R(0);
-#pragma unroll 1
-            for (int s = 0; s < 18; ++s) {
-                int o[3];
-                big_offset_rt(s, o);
-                R row[9];
-                staged_row<R>(sh, geo, g, ih2, Mh, s, pidx(g, i + o[0], j + o[1], k + o[2]), row, m.geof);
+            if constexpr (fold) {
 #pragma unroll
                 for (int v = 0; v < 5; ++v) {
                     const R dq = sh[(54 + 18 * v + s) * RM_BS];
@@ -823,12 +818,15 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
                     for (int n = 0; n < 9; ++n) rhs[v][n] += row[n] * dq;
                 }
             }
+        }
+        chol_factor<R, 9>(N);
+        if constexpr (fold) {
 #pragma unroll
             for (int v = 0; v < 5; ++v) {
                 chol_solve<R, 9>(N, rhs[v]);
-                coef[coef_slot(v, 0) * g.cstride + t] = beta_quadratic_mapped(rhs[v], Mh);
+                beta0[v] = beta_quadratic_mapped(rhs[v], Mh);
 #pragma unroll
-                for (int n = 0; n < 9; ++n) coef[coef_slot(v, 1 + n) * g.cstride + t] = rhs[v][n];
+                for (int n = 0; n < 9; ++n) p0[v][n] = rhs[v][n];
             }
         }
 #pragma unroll 1
@@ -854,9 +852,10 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
             for (int n = 0; n < 9; ++n) coef[coef_slot(v, 1 + n) * g.cstride + t] = a[n];
         }
     }
-    R beta0[5];
+    if constexpr (!fold) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) beta0[v] = coef[coef_slot(v, 0) * g.cstride + t];
+        for (int v = 0; v < 5; ++v) beta0[v] = coef[coef_slot(v, 0) * g.cstride + t];
+    }
     // one pass over the sub-stencils (AoSums): the sums of the nonlinear
     // weights and of the linear part of P~, and the largest
     // |b_x| + |b_y| + |b_z| over the P_m (positivity bound)
@@ -949,7 +948,7 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
 #pragma unroll
         for (int n = 0; n < 9; ++n) {
             R *cp = coef + coef_slot(v, 1 + n) * g.cstride + t;
-            const R a = *cp;
+            const R a = fold ? p0[v][n] : *cp;
             r0 += m_abs(a) * ext[n];
             *cp = iw * (f0 * a + (n < 3 ? lin[n] : R(0)));
         }
