@@ -301,8 +301,8 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
         ok = ok && cudaMalloc((void **)&h->vnext, g.ncell * sizeof(double)) == cudaSuccess;
         h->bytes += tbytes + (hk::NGEO * g.pstride + 2 * g.ncell) * sizeof(double);
         if (ok && grid->precision == HGKS_MIXED) {
-            ok = cudaMalloc((void **)&h->geof, 6 * g.pstride * sizeof(float)) == cudaSuccess;
-            h->bytes += 6 * g.pstride * sizeof(float);
+            ok = cudaMalloc((void **)&h->geof, hk::GEOF * g.pstride * sizeof(float)) == cudaSuccess;
+            h->bytes += hk::GEOF * g.pstride * sizeof(float);
             h->map.geof = h->geof;
             h->map.qsplit = h->Qsplit;
         }

@@ -33,15 +33,19 @@ __global__ void __launch_bounds__(128) k_geom(double *__restrict__ geo, Geo g, M
     }
     double rec[NGEO];
     if constexpr (MIXED) {
-        float fm[6];
+        float fm[GEOF];
         cell_geometry_mixed(m, i, j, k, float(m.amp * Sf), rec, fm);
 #pragma unroll
-        for (int e = 0; e < 6; ++e) m.geof[e * g.pstride + t] = fm[e];
+        for (int e = 0; e < GEOF; ++e) m.geof[e * g.pstride + t] = fm[e];
     } else {
         cell_geometry(m, i, j, k, Sf, rec);
         if (m.geof) {
+            const int idx[3] = {i, j, k};
 #pragma unroll
             for (int e = 0; e < 6; ++e) m.geof[e * g.pstride + t] = float(rec[4 + e]);
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                m.geof[(6 + d) * g.pstride + t] = float(rec[1 + d] - (m.lo[d] + ((double)idx[d] + 0.5) * m.h[d]));
         }
     }
 #pragma unroll

@@ -23,8 +23,9 @@ struct MapGeo {
     float lof[3], hf[3], ihf[3];
     const float *sxf, *syf, *szf;
     // mixed path (null otherwise): an FP32 copy of the cells' central second
-    // moments, [6][pstride], written by the geometry kernel, and the split
-    // state of the stage's Q (Q_hi + Q_lo in FP32, [2][5][pstride])
+    // moments and of their centroid offsets from the reference centres,
+    // [GEOF][pstride], written by the geometry kernel, and the split state
+    // of the stage's Q (Q_hi + Q_lo in FP32, [2][5][pstride])
     float *geof;
     const float *qsplit;
 };
@@ -32,6 +33,9 @@ struct MapGeo {
 // per-cell geometry record (FP64, over the padded cell box): volume,
 // centroid, central second moments (xx, yy, zz, xy, xz, yz)
 constexpr int NGEO = 10;
+// FP32 copy of the mixed path: the six central moments, then the centroid
+// minus the reference centre lo + (idx + 1/2) h (3)
+constexpr int GEOF = 9;
 // reconstruction record per cell (working precision): 5 x (Q_c, 9
 // coefficients) as on the uniform mesh, then the cell frame: centroid (3),
 // h, and the cell means of the quadratic monomials in the scaled frame (6)
@@ -140,7 +144,7 @@ HK_HD void cell_geometry(const MapGeo &m, int i, int j, int k, double S, double 
 // xi_c + offset are assembled in FP64.  fm receives the central moments in
 // FP32 (the copy the FP32 reconstruction reads).
 __device__ __forceinline__ void cell_geometry_mixed(const MapGeo &m, int i, int j, int k, float aS,
-                                                    double out[NGEO], float fm[6])
+                                                    double out[NGEO], float fm[GEOF])
 {
     const float g = float(GAUSS_S);
     float sv[8];
@@ -201,7 +205,10 @@ __device__ __forceinline__ void cell_geometry_mixed(const MapGeo &m, int i, int 
     const int idx[3] = {i, j, k};
     out[0] = m.h[0] * m.h[1] * m.h[2] * double(vr);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) out[1 + d] = (m.lo[d] + ((double)idx[d] + 0.5) * m.h[d]) + double(cy[d]);
+    for (int d = 0; d < 3; ++d) {
+        out[1 + d] = (m.lo[d] + ((double)idx[d] + 0.5) * m.h[d]) + double(cy[d]);
+        fm[6 + d] = cy[d];
+    }
 #pragma unroll
     for (int e = 0; e < 6; ++e) {
         fm[e] = M[e] * ivr;
@@ -759,14 +766,32 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
         }
     }
     // stage the neighbours' scaled centroid offsets (and, mixed, the data
-    // differences)
+    // differences).  Mixed: c_nb - c_c = o h + (off_nb - off_c) with off the
+    // FP32 centroid offsets from the reference centres, all in FP32 (the
+    // terms are of the size of a cell, so this keeps the FP32 rounding of
+    // the FP64 difference)
+    float offc[3] = {0.0f, 0.0f, 0.0f};
+    const float ihf = float(ih);
+    if constexpr (RmStage<R>::dq) {
+        if (m.geof) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) offc[d] = m.geof[(6 + d) * g.pstride + pc];
+        }
+    }
 #pragma unroll 1
     for (int s = 0; s < 18; ++s) {
         int o[3];
         big_offset_rt(s, o);
         const long long pn = pidx(g, i + o[0], j + o[1], k + o[2]);
+        if (RmStage<R>::dq && m.geof) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) sh[(3 * s + d) * RM_BS] = R((geo[(1 + d) * g.pstride + pn] - F.c[d]) * ih);
+            for (int d = 0; d < 3; ++d)
+                sh[(3 * s + d) * RM_BS] =
+                    R((float(o[d]) * m.hf[d] + (m.geof[(6 + d) * g.pstride + pn] - offc[d])) * ihf);
+        } else {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) sh[(3 * s + d) * RM_BS] = R((geo[(1 + d) * g.pstride + pn] - F.c[d]) * ih);
+        }
         if constexpr (RmStage<R>::dq) {
             if (m.qsplit) {
                 // from the split state: (hi_nb - hi_c) + (lo_nb - lo_c)
