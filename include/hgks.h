@@ -281,8 +281,7 @@ void hgks_batch_destroy(hgks_batch_t *b);
  * in it (mixed: also the split state): cubes of up to 27^3 cells in FP64 and 29^3 mixed; larger
  * grids return HGKS_E_INVALID with the byte count in hgks_last_error(NULL).
  * The first call on a device looks up the array's device address with that
- * device current (cudaGetSymbolAddress); make that first call before any
- * stream capture.  Every call shares the one array and overwrites what an
+ * device current (cudaGetSymbolAddress).  Every call shares the one array and overwrites what an
  * earlier call left there (nothing of it is read back), so calls that may
  * overlap on the GPU (other streams, other host threads) race: order them
  * on one stream or serialise them. */
