@@ -7,8 +7,9 @@ path (``paper_1909_01580_gb300``) never does and shares no code with it.
 
 The arithmetic lives in ``hgks_oracle.c`` (compiled with gcc, no FP
 contraction); this module only builds it and marshals NumPy arrays through
-ctypes.  Parity unpinned: the positivity fallback at shocks and the
-Prandtl-number heat-flux correction (see the C header comment).
+ctypes.  The C header comment says how the two parts that the paper's printed
+values do not reach (the positivity fallback, the Prandtl-number correction)
+are pinned.
 """
 from __future__ import annotations
 

@@ -17,9 +17,12 @@
  * can check it against the paper by eye.  Nothing is fused or reordered for
  * speed.  Readings of passages the paper leaves open are marked "Reading:".
  *
- * Parity unpinned: the positivity fallback (Sec. 4 limiter) is pinned only by
- * invariants, and the Prandtl-number heat-flux correction (the paper is
- * silent on it) only by its Pr = 1 no-op.
+ * Pins of the two parts the paper's printed values do not reach: the
+ * positivity fallback (Sec. 4 limiter) by hand-built cells whose candidate
+ * polynomials go negative at exactly one of the 24 Gauss points, or only
+ * between them; the Prandtl-number heat-flux correction (a reading: the
+ * paper is silent on it) by its Pr = 1 no-op and by the Navier-Stokes limit
+ * of the heat flux, -kappa dT/dx with kappa = mu gamma/((gamma - 1) Pr).
  *
  * Layout of every state array crossing this file's interface:
  * conservative cell averages (rho, rho U, rho V, rho W, rho E), SoA
@@ -1016,7 +1019,7 @@ void orc_time_integrals(double delta, double tau, double *q)
  * Reading: eq. (flux) pairs g_r with H(u) and g_l with 1-H(u), at odds with
  * the half-space split of Q0 printed right below it; the split of Q0 is
  * followed (g_l carries u > 0).
- * Reading (Prandtl number, parity unpinned): the energy flux takes the
+ * Reading (Prandtl number; the paper is silent): the energy flux takes the
  * usual correction F_E += (1/Pr - 1) q with q the time-integrated heat flux
  * about the velocity of g0, when mu > 0 and Pr != 1. */
 int orc_point_flux(const orc_cfg *c, const double *in, const double *ug, double dt, double *F, double *dF)
