@@ -108,6 +108,43 @@ def test_reconstruction_parity(case):
         assert np.abs(coef[:, v, :] - ref).max() <= 1e-12 * scale, (case, v)
 
 
+@pytest.mark.parametrize("case", ["ragged_periodic", "two_columns_reflective", "tgv_one_column"])
+def test_mixed_reconstruction_against_oracle(case):
+    """The mixed reconstruction (FP32 from the split state) against the FP64
+    oracle on ragged and reflective boxes (34 x 31 x 9 periodic, 62 x 7 x 6
+    reflective, TGV 30^3): coefficients within 2e-6 of each variable's scale
+    (FP32 arithmetic on differences formed to FP32 round-off; measured
+    2.6e-7); smooth data, so no cell is flagged on either side."""
+    if case == "ragged_periodic":
+        n = (34, 31, 9)
+        lo, hi = _box_for(n, 1.0 / 34)
+        q = W.smooth_random(n, seed=31, lo=lo, hi=hi, amp=0.2)
+        kw = dict()
+    elif case == "two_columns_reflective":
+        n = (62, 7, 6)
+        lo, hi = _box_for(n, 1.0 / 62)
+        q = W.smooth_random(n, seed=32, lo=lo, hi=hi, amp=0.2)
+        kw = dict(bc=(1,) * 6)
+    else:
+        n = (30, 30, 30)
+        q, lo, hi = W.taylor_green(n)
+        kw = dict()
+    cfg = oracle.make_cfg(n, lo, hi, **kw)
+    coef_o, flag_o, _ = oracle.reconstruct(cfg, q)
+    s = _solver(n, lo, hi, precision=hgks.HGKS_MIXED, **kw)
+    s.set_state(q)
+    coef, flag = s.reconstruct()
+    s.close()
+    assert not flag_o.any() and not flag.any()
+    worst = 0.0
+    for v in range(5):
+        ref = coef_o[:, v, 1:]
+        scale = max(np.abs(ref).max(), 1e-300)
+        worst = max(worst, float(np.abs(coef[:, v, :] - ref).max() / scale))
+    print(f"mixed reconstruction {case}: max difference {worst:.3e} of the scale")
+    assert worst <= 2e-6, worst
+
+
 def test_positivity_fallback_fires_and_matches():
     """A near-vacuum pocket makes the linear polynomials negative: the
     fallback fires on the same cells as in the oracle."""
