@@ -39,16 +39,16 @@ UNIT = "cell-stage updates/s"
 # TGV 64^3 x-face launch (smsp__sass_thread_inst_executed_op_{dfma,dadd,dmul,
 # ffma,fadd,fmul}_pred_on over its 1,064,960 Gauss points; 2 flop per FMA):
 #   FP64 path:  1063.2 DFMA + 127.5 DADD + 412.0 DMUL = 2666 flop, 1603 FP64 instructions
-#   mixed path: 970 FFMA + 129 FADD + 421 FMUL        = 2490 flop, 1520 FP32 instructions
+#   mixed path: 984 FFMA + 115 FADD + 415 FMUL        = 2498 flop, 1514 FP32 instructions
 # DRAM bytes per face (read + write) of one launch at 128^3 (inputs larger
 # than L2), from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum`.
-FLUX_FLOP_PER_GP = {"fp64": 2666.0, "mixed": 2490.0}
-FLUX_INST_PER_GP = {"fp64": 1603.0, "mixed": 1520.0}
+FLUX_FLOP_PER_GP = {"fp64": 2666.0, "mixed": 2498.0}
+FLUX_INST_PER_GP = {"fp64": 1603.0, "mixed": 1514.0}
 # x-face launch of TGV 128^3 (2,113,536 faces): FP64 853.71 MB read + 157.55 MB
-# written in 23.84 ms, mixed 511.24 MB + 149.90 MB in 0.523 ms (ncu, cold L2;
+# written in 23.84 ms, mixed 511.25 MB + 151.54 MB in 0.503 ms (ncu, cold L2;
 # the mixed records carry 2 unused floats per variable: 240 B read per face)
 FLUX_TRAFFIC_BYTES_PER_FACE = {"fp64": (853709568 + 157546496) / 2113536,
-                               "mixed": (511239680 + 149897984) / 2113536}
+                               "mixed": (511245568 + 151543296) / 2113536}
 # the algorithmic bytes per face: the two cells' reconstruction records
 # (Q_c and 9 coefficients of 5 variables) read once per face pair of a
 # cell, i.e. one record per face, and the face's 10 FP64 sums written once
