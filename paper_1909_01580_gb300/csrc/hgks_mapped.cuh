@@ -812,14 +812,42 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
     // (0 and 1..9 of each variable)
     constexpr bool fold = RmStage<R>::dq;
     R p0[5][9], beta0[5];
+    if constexpr (!fold) {
+        // FP64: the five right-hand sides A^T dQ in one sweep over the 18
+        // rows (each row formed once for all five), parked in the output
+        // slots; the normal matrix takes a second sweep, since its 45
+        // accumulators and these 45 do not fit in registers together
+        R rhs[5][9];
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+#pragma unroll
+            for (int n = 0; n < 9; ++n) rhs[v][n] = R(0);
+#pragma unroll 1
+        for (int s = 0; s < 18; ++s) {
+            int o[3];
+            big_offset_rt(s, o);
+            const long long pn = pidx(g, i + o[0], j + o[1], k + o[2]);
+            R row[9];
+            staged_row<R>(sh, geo, g, ih2, Mh, s, pn, row, m.geof);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) {
+                const R dq = staged_dq<R>(sh, Q, g, v, s, pn, qcd[v]);
+#pragma unroll
+                for (int n = 0; n < 9; ++n) rhs[v][n] += row[n] * dq;
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v)
+#pragma unroll
+            for (int n = 0; n < 9; ++n) coef[coef_slot(v, 1 + n) * g.cstride + t] = rhs[v][n];
+    }
     {
         R N[45];
 #pragma unroll
         for (int e = 0; e < 45; ++e) N[e] = R(0);
         // FP32: the five right-hand sides A^T dQ gathered in the same sweep
         // over the 18 rows as the normal matrix (each row, and the
-        // neighbour's second moments it reads, formed once); FP64 sweeps
-        // again per variable below
+        // neighbour's second moments it reads, formed once)
         R rhs[5][9];
 #pragma unroll
         for (int v = 0; v < 5; ++v)
@@ -856,21 +884,9 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
         }
 #pragma unroll 1
         for (int v = 0; v < (fold ? 0 : 5); ++v) {
-            const double qc = Q[v * g.pstride + pc];
             R a[9];
 #pragma unroll
-            for (int n = 0; n < 9; ++n) a[n] = R(0);
-#pragma unroll 1
-            for (int s = 0; s < 18; ++s) {
-                int o[3];
-                big_offset_rt(s, o);
-                const long long pn = pidx(g, i + o[0], j + o[1], k + o[2]);
-                R row[9];
-                staged_row<R>(sh, geo, g, ih2, Mh, s, pn, row, m.geof);
-                const R dq = staged_dq<R>(sh, Q, g, v, s, pn, qc);
-#pragma unroll
-                for (int n = 0; n < 9; ++n) a[n] += row[n] * dq;
-            }
+            for (int n = 0; n < 9; ++n) a[n] = coef[coef_slot(v, 1 + n) * g.cstride + t];
             chol_solve<R, 9>(N, a);
             coef[coef_slot(v, 0) * g.cstride + t] = beta_quadratic_mapped(a, Mh);
 #pragma unroll

@@ -44,6 +44,12 @@ def test_invalid_arguments_rejected_before_any_device_work():
     with pytest.raises(hgks.HgksError) as e:
         hgks.hgks_create((4, 4, 4), (0, 0, 0), (1, 1, 1), bc=(0, 1, 0, 0, 0, 0))  # unpaired periodic
     assert e.value.code == hgks.HGKS_E_INVALID
+    with pytest.raises(hgks.HgksError) as e:
+        hgks.hgks_create((1025, 4, 4), (0, 0, 0), (1025, 4, 4))  # beyond HGKS_MAX_CELLS_PER_AXIS = 1024
+    assert e.value.code == hgks.HGKS_E_INVALID
+    with pytest.raises(hgks.HgksError) as e:
+        hgks.hgks_create((2, 8, 8), (0, 0, 0), (2, 8, 8), bc=(1, 1, 0, 0, 0, 0))  # reflective axis of 2 cells
+    assert e.value.code == hgks.HGKS_E_INVALID
 
 
 def test_no_cpu_fallback_without_gpu():

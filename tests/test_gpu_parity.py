@@ -472,6 +472,26 @@ def test_smallest_periodic_grid_parity():
     assert max_rel(q, qo) <= TOL
 
 
+@pytest.mark.parametrize("precision", [hgks.HGKS_FP64, hgks.HGKS_MIXED])
+def test_longest_axis_parity(precision):
+    """The largest extent an axis may have (HGKS_MAX_CELLS_PER_AXIS = 1024
+    cells) on a thin periodic box, 1024 x 3 x 2: two fixed-dt steps against
+    the oracle (FP64 at the parity bar, mixed at the FP32 bar of the 16^3
+    TGV test)."""
+    n = (1024, 3, 2)
+    lo, hi = _box_for(n, 1.0 / 64)
+    q0 = W.smooth_random(n, seed=41, lo=lo, hi=hi, amp=0.2)
+    cfg = oracle.make_cfg(n, lo, hi)
+    dt = oracle.cfl_dt(cfg, q0, 0.35)
+    qo, _, _, _ = oracle.step(cfg, q0, 0.0, 2, dt_fixed=dt)
+    s = _solver(n, lo, hi, precision=precision)
+    s.set_state(q0)
+    s.step(2, dt_fixed=dt)
+    q, _ = s.get_state()
+    s.close()
+    assert max_rel(q, qo) <= (TOL if precision == hgks.HGKS_FP64 else 1e-4), max_rel(q, qo)
+
+
 def test_zero_steps_and_t_end_stop():
     n = (8, 8, 8)
     q0 = W.density_advection(n)
