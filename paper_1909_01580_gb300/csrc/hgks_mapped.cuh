@@ -38,7 +38,7 @@ constexpr int NGEO = 10;
 constexpr int GEOF = 9;
 // reconstruction record per cell (working precision): 5 x (Q_c, 9
 // coefficients) as on the uniform mesh, then the cell frame: centroid (3),
-// h, and the cell means of the quadratic monomials in the scaled frame (6)
+// 1/h, and the cell means of the quadratic monomials in the scaled frame (6)
 constexpr int NCOEF_M = 60;
 constexpr int SLOT_FRAME = 50;
 
@@ -1004,7 +1004,7 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
     coef[(SLOT_FRAME + 0) * g.cstride + t] = R(F.c[0]);
     coef[(SLOT_FRAME + 1) * g.cstride + t] = R(F.c[1]);
     coef[(SLOT_FRAME + 2) * g.cstride + t] = R(F.c[2]);
-    coef[(SLOT_FRAME + 3) * g.cstride + t] = R(F.h);
+    coef[(SLOT_FRAME + 3) * g.cstride + t] = R(ih);
 #pragma unroll
     for (int e = 0; e < 6; ++e) coef[(SLOT_FRAME + 4 + e) * g.cstride + t] = Mh[e];
 }
@@ -1047,13 +1047,12 @@ template <typename R>
 __device__ __forceinline__ void eval_cell_mapped(const R *__restrict__ coef, const Geo &g, long long ci,
                                                  const R xg[3], R val[5], R grad[5][3])
 {
-    R c[3], h, Mh[6];
+    R c[3], Mh[6];
 #pragma unroll
     for (int e = 0; e < 3; ++e) c[e] = coef[(SLOT_FRAME + e) * g.cstride + ci];
-    h = coef[(SLOT_FRAME + 3) * g.cstride + ci];
+    const R ih = coef[(SLOT_FRAME + 3) * g.cstride + ci];
 #pragma unroll
     for (int e = 0; e < 6; ++e) Mh[e] = coef[(SLOT_FRAME + 4 + e) * g.cstride + ci];
-    const R ih = R(1) / h;
     const R X[3] = {(xg[0] - c[0]) * ih, (xg[1] - c[1]) * ih, (xg[2] - c[2]) * ih};
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
@@ -1133,9 +1132,10 @@ __device__ __forceinline__ void flux_mapped_item(const R *__restrict__ coef, dou
         }
     }
     const R nrm[3] = {Xa[1] * Xb[2] - Xa[2] * Xb[1], Xa[2] * Xb[0] - Xa[0] * Xb[2], Xa[0] * Xb[1] - Xa[1] * Xb[0]};
-    const R area = m_sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
-    const R iarea = R(1) / area;
-    const R ilb = R(1) / m_sqrt(Xb[0] * Xb[0] + Xb[1] * Xb[1] + Xb[2] * Xb[2]);
+    // |n| and 1/|n| from one reciprocal square root (no division)
+    const R nn = nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2];
+    const R iarea = m_rsqrt(nn), area = nn * iarea;
+    const R ilb = m_rsqrt(Xb[0] * Xb[0] + Xb[1] * Xb[1] + Xb[2] * Xb[2]);
     R fr[3][3];
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
