@@ -290,14 +290,19 @@ def run_gpu(args, rank, world, local, dist):
             "t_reached": t_now,
             "op_block": op_block,
         }
-        # end to end through the C ABI with host buffers: every step copies the
-        # state in from pinned host memory and the result back out
+        # end to end through the C ABI with host buffers: every step loads the
+        # state from pinned host memory and reads the result back out (the
+        # library's kernels read and write the pinned buffers directly)
         if not args.no_e2e:
             qh = torch.from_numpy(q0).pin_memory()
             qh_np = qh.numpy()
             out = torch.empty_like(qh).pin_memory()
             out_np = out.numpy()
             e2e_steps = max(1, min(args.steps, 5))
+            # one untimed pass of the same calls first
+            hgks.hgks_set_state(s.h, qh_np, 0.0)
+            s.step(1, cfl=0.35)
+            hgks.hgks_get_state(s.h, out_np)
             barrier()
             t0 = time.perf_counter()
             for _ in range(e2e_steps):

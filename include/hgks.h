@@ -115,7 +115,13 @@ int hgks_create(const hgks_grid_t *grid, double gamma, double mu, double Pr, con
  * the characteristic buffers cannot be allocated. */
 int hgks_set_option(hgks_t *h, const char *key, double value);
 
-/* Load the state q ([5][nz][ny][nx] FP64, copied) at time t.  On a mapped
+/* Load the state q ([5][nz][ny][nx] FP64, copied) at time t.  on_device: 1
+ * when q is device memory (ordered on the handle's stream, no
+ * synchronisation), 0 for host memory (the call returns once q has been
+ * read).  Host memory that the GPU can address (pinned or registered:
+ * cudaHostAlloc, cudaHostRegister) is read by the kernel that lays the state
+ * out, over the host link; other host memory is copied to a device buffer
+ * first.  On a mapped
  * mesh the cell volumes that the update divides by restart from the
  * geometric volumes of the mesh at t.  On a moving mesh each step freezes
  * the geometry at the start of each stage (t_n, then t_n + dt/2), takes the
@@ -125,7 +131,10 @@ int hgks_set_option(hgks_t *h, const char *key, double value);
 int hgks_set_state(hgks_t *h, const double *q, int on_device, double t);
 
 /* Copy the state out into q ([5][nz][ny][nx] FP64) and the time into *t
- * (t may be NULL). */
+ * (t may be NULL).  on_device as for hgks_set_state: host memory that the
+ * GPU can address is written by the kernel that gathers the interior, other
+ * host memory through a device buffer; with host memory (or t) the call
+ * returns once q (and *t) hold the state. */
 int hgks_get_state(hgks_t *h, double *q, int on_device, double *t);
 
 /* Advance nsteps two-stage fourth-order steps (Sec. 3):

@@ -423,14 +423,31 @@ extern "C" int hgks_set_option(hgks_t *h, const char *key, double value)
     return HGKS_OK;
 }
 
+// the device address of a host buffer that the GPU can address directly
+// (pinned or registered host memory), or null (pageable memory)
+static void *addressable_host(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 extern "C" int hgks_set_state(hgks_t *h, const double *q, int on_device, double t)
 {
     if (!h || !q) return HGKS_E_INVALID;
     const Geo &g = h->g;
     const double *src = q;
     if (!on_device) {
-        CUDA_OK(h, cudaMemcpyAsync(h->Wacc, q, 5 * g.ncell * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-        src = h->Wacc;
+        // addressable host memory: the scatter kernel reads it over the host
+        // link; otherwise a copy to the device buffer first
+        src = static_cast<const double *>(addressable_host(q));
+        if (!src) {
+            CUDA_OK(h, cudaMemcpyAsync(h->Wacc, q, 5 * g.ncell * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+            src = h->Wacc;
+        }
     }
     hk::launch_scatter(src, h->Qn, g, h->stream);
     hk::launch_init_ctl(h->ctl, t, h->stream);
@@ -453,11 +470,14 @@ extern "C" int hgks_get_state(hgks_t *h, double *q, int on_device, double *t)
     if (!h || !q) return HGKS_E_INVALID;
     if (!h->have_state) return fail(h, HGKS_E_STATE, "no state loaded%s");
     const Geo &g = h->g;
-    double *dst = on_device ? q : h->Wacc;
+    // addressable host memory: the gather kernel writes it over the host
+    // link; otherwise through the device buffer
+    double *mapped = on_device ? nullptr : static_cast<double *>(addressable_host(q));
+    double *dst = on_device ? q : (mapped ? mapped : h->Wacc);
     hk::launch_gather(h->Qn, dst, g, h->stream);
     int rc = check_launch(h, 1);
     if (rc) return rc;
-    if (!on_device)
+    if (!on_device && !mapped)
         CUDA_OK(h, cudaMemcpyAsync(q, h->Wacc, 5 * g.ncell * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     if (t) {
         CUDA_OK(h, cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
