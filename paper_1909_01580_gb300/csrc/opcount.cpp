@@ -9,7 +9,7 @@
 #include "hgks_device.cuh"
 
 struct Counts {
-    long add = 0, mul = 0, div = 0, sqrt = 0, rsqrt = 0, exp = 0, expm1 = 0, erfc = 0, pow = 0;
+    long add = 0, mul = 0, div = 0, sqrt = 0, rsqrt = 0, exp = 0, expm1 = 0, erfc = 0, log = 0;
     void reset() { *this = Counts(); }
 };
 static Counts C;
@@ -32,7 +32,7 @@ inline bool operator>(CR a, CR b) { return a.v > b.v; }
 inline CR m_exp(CR a) { ++C.exp; return CR(std::exp(a.v)); }
 inline CR m_expm1(CR a) { ++C.expm1; return CR(std::expm1(a.v)); }
 inline CR m_erfc(CR a) { ++C.erfc; return CR(std::erfc(a.v)); }
-inline CR m_pow(CR a, CR b) { ++C.pow; return CR(std::pow(a.v, b.v)); }
+inline CR m_log(CR a) { ++C.log; return CR(std::log(a.v)); }
 inline CR m_sqrt(CR a) { ++C.sqrt; return CR(std::sqrt(a.v)); }
 inline CR m_rsqrt(CR a) { ++C.rsqrt; return CR(1.0 / std::sqrt(a.v)); }
 inline CR m_abs(CR a) { return CR(std::fabs(a.v)); }

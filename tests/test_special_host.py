@@ -1,6 +1,7 @@
 """Host check of erfc_half, the error function complement of the
 half-space moments (Sec. 3) in the device header: for |x| < 3/4 it sums the
-Maclaurin series of erf, elsewhere it calls the library's erfc.  Against the
+Maclaurin series of erf, elsewhere it calls the library's erfc; and of
+pow_pos, the power of the viscosity law (Sec. 4 turbulence case).  Against the
 C library's long-double erfc it must stay within a few units in the last
 place: FP64 <= 1e-15 (measured 5.3e-16), FP32 <= 6e-7, ten units (measured
 4.0e-7 in the host build, which rounds every product and sum without fused
@@ -24,7 +25,12 @@ def test_erfc_half_matches_the_library_erfc(tmp_path):
     assert r.returncode == 0, r.stderr
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
     assert out.returncode == 0, out.stderr
-    d64_series, d64_all, f32_series, f32_all = (float(v) for v in out.stdout.split())
+    d64_series, d64_all, f32_series, f32_all, pow64, pow32 = (float(v) for v in out.stdout.split())
     print("erfc_half relative error: FP64", d64_series, d64_all, "FP32", f32_series, f32_all)
     assert d64_series <= 1e-15 and d64_all <= 1e-15
     assert f32_series <= 6e-7 and f32_all <= 6e-7
+    # the viscosity law's power x^0.76 as exp(0.76 log x) over [1/4, 4]:
+    # within a few units in the last place of the long-double pow (measured
+    # 2.7e-16 and 1.4e-7 with the host's exp and log)
+    print("pow_pos relative error: FP64", pow64, "FP32", pow32)
+    assert pow64 <= 6e-16 and pow32 <= 3e-7
