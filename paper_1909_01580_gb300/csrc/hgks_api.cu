@@ -26,7 +26,7 @@ struct hgks {
     bool own_stream;
     int device;
     double *Qn, *Qs, *Wacc;      // padded Q^n, padded Q*, accumulator / staging [5][ncell]
-    void *coef;                  // uniform mesh: [cstride] records Rec<R>; mapped: [NCOEF_M][cstride]
+    void *coef;                  // [cstride] records: Rec<R> (uniform mesh), MRec<R> (mapped)
     unsigned char *flag;         // [cstride]
     double *F[3];                // face fluxes [10][nface_d]
     Ctl *ctl;                    // device control block
@@ -257,8 +257,9 @@ extern "C" int hgks_create(const hgks_grid_t *grid, double gamma, double mu, dou
     const size_t rsz = grid->precision == HGKS_MIXED ? sizeof(float) : sizeof(double);
     h->mesh = grid->mesh;
     const bool mapped = h->mesh != 0;
-    const int ncoef = mapped ? hk::NCOEF_M
-                             : (grid->precision == HGKS_MIXED ? hk::Rec<float>::N : hk::Rec<double>::N);
+    const bool f32 = grid->precision == HGKS_MIXED;
+    const int ncoef = mapped ? (f32 ? hk::MRec<float>::N : hk::MRec<double>::N)
+                             : (f32 ? hk::Rec<float>::N : hk::Rec<double>::N);
     const int nfv = mapped ? hk::NFACE_M : 10;
     size_t sizes[] = {5 * g.pstride * sizeof(double), 5 * g.pstride * sizeof(double), 5 * g.ncell * sizeof(double),
                       ncoef * g.cstride * rsz, (size_t)g.cstride};

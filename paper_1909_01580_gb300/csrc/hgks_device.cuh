@@ -168,6 +168,21 @@ template <typename R> HK_HD long long rec_idx(long long cell, int v, int n)
     return cell * Rec<R>::N + v * Rec<R>::VS + n;
 }
 
+// One record per cell of a mapped mesh: the cell frame (centroid (3), 1/h,
+// the cell means of the quadratic monomials in the scaled frame (6)) at
+// 0 .. 9, then variable v's 10 values (Q_c, the 9 coefficients of P~ - Q_c)
+// at VS (1 + v) .. VS (1 + v) + 9; every part on a 16-byte boundary (FP32:
+// 12 floats with 2 unused; FP64: 10 doubles), so that the face flux reads a
+// cell with vector loads at constant offsets.
+template <typename R> struct MRec {
+    static constexpr int VS = sizeof(R) == 4 ? 12 : 10;
+    static constexpr int N = 6 * VS;
+};
+template <typename R> HK_HD long long mrec_idx(long long cell, int v, int n)
+{
+    return cell * MRec<R>::N + MRec<R>::VS * (1 + v) + n;
+}
+
 // Per-handle device control block: time, step and status.
 struct Ctl {
     double t, dt;

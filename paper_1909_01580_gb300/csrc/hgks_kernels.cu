@@ -151,8 +151,7 @@ __global__ void k_export_coef(const R *__restrict__ coef, const unsigned char *_
     const long long ci = cidx(g, i, j, k);
     for (int v = 0; v < 5; ++v)
         for (int n = 0; n < 9; ++n)
-            out[t * 45 + v * 9 + n] =
-                double(rec ? coef[rec_idx<R>(ci, v, 1 + n)] : coef[coef_slot(v, 1 + n) * g.cstride + ci]);
+            out[t * 45 + v * 9 + n] = double(rec ? coef[rec_idx<R>(ci, v, 1 + n)] : coef[mrec_idx<R>(ci, v, 1 + n)]);
     if (oflag) oflag[t] = flag[ci];
 }
 

@@ -36,11 +36,40 @@ constexpr int NGEO = 10;
 // FP32 copy of the mixed path: the six central moments, then the centroid
 // minus the reference centre lo + (idx + 1/2) h (3)
 constexpr int GEOF = 9;
-// reconstruction record per cell (working precision): 5 x (Q_c, 9
-// coefficients) as on the uniform mesh, then the cell frame: centroid (3),
-// 1/h, and the cell means of the quadratic monomials in the scaled frame (6)
-constexpr int NCOEF_M = 60;
-constexpr int SLOT_FRAME = 50;
+
+// one 16-byte-aligned part of a mapped record (the frame, or one
+// variable: MRec<R>::VS values) by vector loads and stores
+__device__ __forceinline__ void load_mrec_part(const float *__restrict__ p, float x[12])
+{
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+    x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    x[8] = c.x; x[9] = c.y; x[10] = c.z; x[11] = c.w;
+}
+__device__ __forceinline__ void load_mrec_part(const double *__restrict__ p, double x[10])
+{
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+    for (int e = 0; e < 5; ++e) {
+        const double2 a = __ldg(q + e);
+        x[2 * e] = a.x;
+        x[2 * e + 1] = a.y;
+    }
+}
+__device__ __forceinline__ void store_mrec_part(float *__restrict__ p, const float x[12])
+{
+    float4 *q = reinterpret_cast<float4 *>(p);
+    q[0] = make_float4(x[0], x[1], x[2], x[3]);
+    q[1] = make_float4(x[4], x[5], x[6], x[7]);
+    q[2] = make_float4(x[8], x[9], x[10], x[11]);
+}
+__device__ __forceinline__ void store_mrec_part(double *__restrict__ p, const double x[10])
+{
+    double2 *q = reinterpret_cast<double2 *>(p);
+#pragma unroll
+    for (int e = 0; e < 5; ++e) q[e] = make_double2(x[2 * e], x[2 * e + 1]);
+}
 
 HK_HD double map_factor(const MapGeo &m, double t) { return m.moving ? sin(m.omega * t) : 1.0; }
 
@@ -839,7 +868,7 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
 #pragma unroll
         for (int v = 0; v < 5; ++v)
 #pragma unroll
-            for (int n = 0; n < 9; ++n) coef[coef_slot(v, 1 + n) * g.cstride + t] = rhs[v][n];
+            for (int n = 0; n < 9; ++n) coef[mrec_idx<R>(t, v, 1 + n)] = rhs[v][n];
     }
     {
         R N[45];
@@ -886,16 +915,16 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
         for (int v = 0; v < (fold ? 0 : 5); ++v) {
             R a[9];
 #pragma unroll
-            for (int n = 0; n < 9; ++n) a[n] = coef[coef_slot(v, 1 + n) * g.cstride + t];
+            for (int n = 0; n < 9; ++n) a[n] = coef[mrec_idx<R>(t, v, 1 + n)];
             chol_solve<R, 9>(N, a);
-            coef[coef_slot(v, 0) * g.cstride + t] = beta_quadratic_mapped(a, Mh);
+            coef[mrec_idx<R>(t, v, 0)] = beta_quadratic_mapped(a, Mh);
 #pragma unroll
-            for (int n = 0; n < 9; ++n) coef[coef_slot(v, 1 + n) * g.cstride + t] = a[n];
+            for (int n = 0; n < 9; ++n) coef[mrec_idx<R>(t, v, 1 + n)] = a[n];
         }
     }
     if constexpr (!fold) {
 #pragma unroll
-        for (int v = 0; v < 5; ++v) beta0[v] = coef[coef_slot(v, 0) * g.cstride + t];
+        for (int v = 0; v < 5; ++v) beta0[v] = coef[mrec_idx<R>(t, v, 0)];
     }
     // one pass over the sub-stencils (AoSums): the sums of the nonlinear
     // weights and of the linear part of P~, and the largest
@@ -984,15 +1013,18 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
     for (int v = 0; v < 5; ++v) {
         R iw, f0, lin[3];
         acc[v].template combine<24>(g0, gm, iw, f0, lin);
-        coef[coef_slot(v, 0) * g.cstride + t] = qcv[v];
+        R out[MRec<R>::VS];
+        out[0] = qcv[v];
         R r0 = R(0);
 #pragma unroll
         for (int n = 0; n < 9; ++n) {
-            R *cp = coef + coef_slot(v, 1 + n) * g.cstride + t;
-            const R a = fold ? p0[v][n] : *cp;
+            const R a = fold ? p0[v][n] : coef[mrec_idx<R>(t, v, 1 + n)];
             r0 += m_abs(a) * ext[n];
-            *cp = iw * (f0 * a + (n < 3 ? lin[n] : R(0)));
+            out[1 + n] = iw * (f0 * a + (n < 3 ? lin[n] : R(0)));
         }
+#pragma unroll
+        for (int n = 10; n < MRec<R>::VS; ++n) out[n] = R(0);
+        store_mrec_part(coef + mrec_idx<R>(t, v, 0), out);
         // bound of |P_m - Q_c| at the Gauss points for all 25 P_m
         rad[v] = m_max(r0, bsum[v] * xmax) * R(1.0000001);
     }
@@ -1001,12 +1033,18 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
     // that its registers do not weigh on this one)
     flag[t] = (Sch.limiter && !positivity_certain(qcv, rad, R(Sch.gamma))) ? 2 : 0;
     // the cell frame for the flux kernels
-    coef[(SLOT_FRAME + 0) * g.cstride + t] = R(F.c[0]);
-    coef[(SLOT_FRAME + 1) * g.cstride + t] = R(F.c[1]);
-    coef[(SLOT_FRAME + 2) * g.cstride + t] = R(F.c[2]);
-    coef[(SLOT_FRAME + 3) * g.cstride + t] = R(ih);
+    {
+        R fr[MRec<R>::VS];
+        fr[0] = R(F.c[0]);
+        fr[1] = R(F.c[1]);
+        fr[2] = R(F.c[2]);
+        fr[3] = R(ih);
 #pragma unroll
-    for (int e = 0; e < 6; ++e) coef[(SLOT_FRAME + 4 + e) * g.cstride + t] = Mh[e];
+        for (int e = 0; e < 6; ++e) fr[4 + e] = Mh[e];
+#pragma unroll
+        for (int n = 10; n < MRec<R>::VS; ++n) fr[n] = R(0);
+        store_mrec_part(coef + t * MRec<R>::N, fr);
+    }
 }
 
 // literal positivity check of the cells marked 2 by recon_mapped_item: all
@@ -1029,7 +1067,7 @@ __device__ __forceinline__ void positivity_mapped_item(const double *__restrict_
     const bool bad = positivity_violated_mapped<R>(Q, geo, g, m, S, i, j, k, F, R(Sch.gamma));
     if (bad) {
         for (int v = 0; v < 5; ++v)
-            for (int n = 1; n < 10; ++n) coef[coef_slot(v, n) * g.cstride + t] = R(0);
+            for (int n = 1; n < 10; ++n) coef[mrec_idx<R>(t, v, n)] = R(0);
         atomicAdd(&ctl->flagged, 1);
     }
     flag[t] = bad ? 1 : 0;
@@ -1047,19 +1085,18 @@ template <typename R>
 __device__ __forceinline__ void eval_cell_mapped(const R *__restrict__ coef, const Geo &g, long long ci,
                                                  const R xg[3], R val[5], R grad[5][3])
 {
-    R c[3], Mh[6];
-#pragma unroll
-    for (int e = 0; e < 3; ++e) c[e] = coef[(SLOT_FRAME + e) * g.cstride + ci];
-    const R ih = coef[(SLOT_FRAME + 3) * g.cstride + ci];
-#pragma unroll
-    for (int e = 0; e < 6; ++e) Mh[e] = coef[(SLOT_FRAME + 4 + e) * g.cstride + ci];
+    R fr[MRec<R>::VS];
+    load_mrec_part(coef + ci * MRec<R>::N, fr);
+    const R c[3] = {fr[0], fr[1], fr[2]}, ih = fr[3];
+    const R Mh[6] = {fr[4], fr[5], fr[6], fr[7], fr[8], fr[9]};
     const R X[3] = {(xg[0] - c[0]) * ih, (xg[1] - c[1]) * ih, (xg[2] - c[2]) * ih};
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-        R a[9];
+        R part[MRec<R>::VS], a[9];
+        load_mrec_part(coef + mrec_idx<R>(ci, v, 0), part);
 #pragma unroll
-        for (int n = 0; n < 9; ++n) a[n] = coef[coef_slot(v, 1 + n) * g.cstride + ci];
-        val[v] = coef[coef_slot(v, 0) * g.cstride + ci] + poly9_mapped(a, X, Mh);
+        for (int n = 0; n < 9; ++n) a[n] = part[1 + n];
+        val[v] = part[0] + poly9_mapped(a, X, Mh);
         grad[v][0] = (a[0] + R(2) * a[3] * X[0] + a[6] * X[1] + a[7] * X[2]) * ih;
         grad[v][1] = (a[1] + R(2) * a[4] * X[1] + a[6] * X[0] + a[8] * X[2]) * ih;
         grad[v][2] = (a[2] + R(2) * a[5] * X[2] + a[7] * X[0] + a[8] * X[1]) * ih;
