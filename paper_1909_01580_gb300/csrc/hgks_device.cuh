@@ -3,6 +3,7 @@
 // flux at a Gauss point (Sec. 3).  Everything is templated on the working
 // precision R (double for the FP64 path, float for the mixed path).
 #pragma once
+#include <string.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -138,6 +139,77 @@ HK_HD void split3(long long t, int a, int b, int &i, int &j, int &k)
     i = (int)(u - r * ua);
     k = (int)(r / ub);
     j = (int)(r - (unsigned)k * ub);
+}
+
+// The split q = hi + lo of the mixed path, hi = fl32(q), lo = fl32(q - hi)
+// (q - hi is exact in FP64), from the IEEE 754 bit fields of q with integer
+// operations where hi and lo are both normal FP32 numbers (unbiased exponent
+// of q in [-72, 126]); elsewhere (zeros, tiny or huge values, infinities,
+// NaNs) by the FP64 arithmetic it replaces.  With q = M 2^(e-52), M the
+// 53-bit significand: hi keeps the top 24 bits of M rounded to nearest,
+// ties to even (a carry out renormalises); the residual q - hi is
+// R 2^(e-52) with R the dropped 29 bits, minus 2^29 when hi rounded up, and
+// lo is R rounded the same way to 24 bits.  The two FP32 conversions and
+// the FP64 subtraction of the plain form run on this GPU's FP64 pipe.
+HK_HD void split_f64(double q, float &hi, float &lo)
+{
+#ifdef __CUDA_ARCH__
+    const unsigned long long b = (unsigned long long)__double_as_longlong(q);
+#else
+    unsigned long long b;
+    memcpy(&b, &q, 8);
+#endif
+    const int e = (int)((b >> 52) & 0x7ffu) - 1023;
+    if (e < -72 || e > 126) {
+        hi = float(q);
+        lo = float(q - double(hi));
+        return;
+    }
+    const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+    const unsigned long long M = (b & 0xfffffffffffffull) | (1ull << 52);
+    const unsigned drop = (unsigned)(M & 0x1fffffffu);  // the low 29 bits
+    unsigned kept = (unsigned)(M >> 29);                 // 24 bits, top bit set
+    const bool up = drop > 0x10000000u || (drop == 0x10000000u && (kept & 1u));
+    int eh = e;
+    kept += up ? 1u : 0u;
+    if (kept == (1u << 24)) {
+        kept = 1u << 23;
+        eh += 1;
+    }
+    const unsigned hb = sgn | ((unsigned)(eh + 127) << 23) | (kept & 0x7fffffu);
+    // residual R 2^(e-52), |R| <= 2^28
+    const int R = up ? (int)drop - (1 << 29) : (int)drop;
+    unsigned lb = 0u;  // R = 0: q - hi = +0
+    if (R != 0) {
+        unsigned A = (unsigned)(R < 0 ? -R : R);
+        const unsigned ls = (R < 0) ? (sgn ^ 0x80000000u) : sgn;
+#ifdef __CUDA_ARCH__
+        int P = 31 - __clz(A);
+#else
+        int P = 31 - __builtin_clz(A);
+#endif
+        unsigned k2;
+        if (P > 23) {
+            const int sh = P - 23;
+            const unsigned d2 = A & ((1u << sh) - 1u), half = 1u << (sh - 1);
+            k2 = A >> sh;
+            k2 += (d2 > half || (d2 == half && (k2 & 1u))) ? 1u : 0u;
+            if (k2 == (1u << 24)) {
+                k2 = 1u << 23;
+                P += 1;
+            }
+        } else {
+            k2 = A << (23 - P);
+        }
+        lb = ls | ((unsigned)(e - 52 + P + 127) << 23) | (k2 & 0x7fffffu);
+    }
+#ifdef __CUDA_ARCH__
+    hi = __uint_as_float(hb);
+    lo = __uint_as_float(lb);
+#else
+    memcpy(&hi, &hb, 4);
+    memcpy(&lo, &lb, 4);
+#endif
 }
 
 HK_HD long long cidx(const Geo &g, int i, int j, int k)

@@ -85,15 +85,32 @@ __device__ __forceinline__ void load_stencil(const double *__restrict__ Qv, cons
 // difference to about one FP32 rounding: the hi part is exact for values
 // within a factor 2 of each other (and otherwise rounds at the size of the
 // result), the lo part is 2^-24 smaller.  The reconstruction then needs no
-// FP64 arithmetic; the split is formed once per stage by k_split.
+// FP64 arithmetic; the split is formed once per stage by k_split, from the
+// bit fields of Q on the integer pipe (split_f64).
+// SPLIT_PER: values per thread; a block of bs threads splits the
+// SPLIT_PER bs consecutive values from b, value b + threadIdx.x + j bs in
+// its j-th pass (coalesced, the SPLIT_PER loads of a thread independent, so
+// that enough bytes are in flight to stream Q)
+constexpr int SPLIT_PER = 4;
 __device__ __forceinline__ void split_item(const double *__restrict__ Q, float *__restrict__ hi,
-                                           float *__restrict__ lo, long long n, long long t)
+                                           float *__restrict__ lo, long long n, long long b)
 {
-    if (t >= n) return;
-    const double q = Q[t];
-    const float h = float(q);
-    hi[t] = h;
-    lo[t] = float(q - double(h));
+    double q[SPLIT_PER];
+#pragma unroll
+    for (int j = 0; j < SPLIT_PER; ++j) {
+        const long long t = b + threadIdx.x + (long long)j * blockDim.x;
+        q[j] = t < n ? Q[t] : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < SPLIT_PER; ++j) {
+        const long long t = b + threadIdx.x + (long long)j * blockDim.x;
+        if (t < n) {
+            float h, l;
+            split_f64(q[j], h, l);
+            hi[t] = h;
+            lo[t] = l;
+        }
+    }
 }
 
 // the stencil differences of one variable from the split state

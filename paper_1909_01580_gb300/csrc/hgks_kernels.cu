@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(128) k_recon(const double *__restrict__ Q, R *
 
 __global__ void k_split(const double *__restrict__ Q, float *__restrict__ hi, float *__restrict__ lo, long long n)
 {
-    split_item(Q, hi, lo, n, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    split_item(Q, hi, lo, n, (long long)blockIdx.x * blockDim.x * SPLIT_PER);
 }
 
 // the literal positivity check of the listed cells: persistent warps that
@@ -232,7 +232,7 @@ void launch_recon(const double *Q, R *coef, unsigned char *flag, const Geo &g, c
     cudaMemsetAsync(&ctl->nmarked, 0, sizeof(unsigned), s);
     if (split) {
         const long long n = 5 * g.pstride;
-        k_split<<<blocks_for(n, 256), 256, 0, s>>>(Q, split, split + n, n);
+        k_split<<<blocks_for(n, 256 * SPLIT_PER), 256, 0, s>>>(Q, split, split + n, n);
     }
     const int smem = 128 * Rec<R>::N * (int)sizeof(R);  // 30 KB FP32, 50 KB FP64 (opted in at first use)
     // the attribute is per device: set once per device and kernel

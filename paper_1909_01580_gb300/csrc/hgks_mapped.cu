@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(RM_BS, MapReconOcc<R>::blocks) k_recon_mapped(
 __global__ void k_split_mapped(const double *__restrict__ Q, float *__restrict__ hi, float *__restrict__ lo,
                                long long n)
 {
-    split_item(Q, hi, lo, n, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    split_item(Q, hi, lo, n, (long long)blockIdx.x * blockDim.x * SPLIT_PER);
 }
 
 template <typename R>
@@ -207,7 +207,7 @@ void launch_recon_mapped(const double *Q, const double *geo, R *coef, unsigned c
 {
     if (sizeof(R) == 4 && m.qsplit) {
         const long long n = 5 * g.pstride;
-        k_split_mapped<<<nblk(n, 256), 256, 0, s>>>(Q, (float *)m.qsplit, (float *)m.qsplit + n, n);
+        k_split_mapped<<<nblk(n, 256 * SPLIT_PER), 256, 0, s>>>(Q, (float *)m.qsplit, (float *)m.qsplit + n, n);
     }
     k_recon_mapped<R><<<nblk(g.cstride, RM_BS), RM_BS, 0, s>>>(Q, geo, coef, flag, g, m, S, ctl, half);
     k_positivity_mapped<R><<<nblk(g.cstride, 128), 128, 0, s>>>(Q, geo, coef, flag, g, m, S, ctl, half);
