@@ -18,11 +18,10 @@ namespace hk {
 // edge and corner ghosts; every ghost reads its interior source directly, so
 // one pass fills all of them.  t: padded linear index.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void halo_item(double *__restrict__ Q, const Geo &g, long long t)
+// the cell at padded coordinates (ip, jp, kp): nothing for an interior cell
+__device__ __forceinline__ void halo_cell(double *__restrict__ Q, const Geo &g, int ip, int jp, int kp)
 {
-    if (t >= g.pstride) return;
-    int ip, jp, kp;
-    split3(t, g.px, g.py, ip, jp, kp);
+    const long long t = ((long long)kp * g.py + jp) * g.px + ip;
     const int idx[3] = {ip - GHOST, jp - GHOST, kp - GHOST};
     const int n[3] = {g.nx, g.ny, g.nz};
     int src[3];
@@ -53,6 +52,49 @@ __device__ __forceinline__ void halo_item(double *__restrict__ Q, const Geo &g, 
         double val = Q[v * g.pstride + from];
         if (v >= 1 && v <= 3 && flip[v - 1]) val = -val;
         Q[v * g.pstride + t] = val;
+    }
+}
+
+// t: padded linear index
+__device__ __forceinline__ void halo_item(double *__restrict__ Q, const Geo &g, long long t)
+{
+    if (t >= g.pstride) return;
+    int ip, jp, kp;
+    split3(t, g.px, g.py, ip, jp, kp);
+    halo_cell(Q, g, ip, jp, kp);
+}
+
+// ghost cells of the padded box, numbered u = 0 .. ghost_count - 1: the
+// z-slabs (the GHOST whole padded planes below and above the interior),
+// then the y-slabs of the interior planes (GHOST whole padded rows below and
+// above the interior rows), then the x-slabs of the interior rows (GHOST
+// cells at each end); (ip, jp, kp) padded coordinates
+__device__ __forceinline__ long long ghost_count(const Geo &g)
+{
+    return g.pstride - (long long)g.nx * g.ny * g.nz;
+}
+__device__ __forceinline__ void ghost_cell(const Geo &g, long long u, int &ip, int &jp, int &kp)
+{
+    const unsigned G2 = 2u * GHOST, px = (unsigned)g.px, py = (unsigned)g.py;
+    const long long zs = (long long)G2 * py * px, ys = (long long)G2 * px * g.nz;
+    if (u < zs) {
+        const unsigned uu = (unsigned)u, plane = px * py;
+        const unsigned kk = uu / plane, r = uu - kk * plane, j = r / px;
+        ip = (int)(r - j * px);
+        jp = (int)j;
+        kp = kk < GHOST ? (int)kk : g.nz + (int)kk;
+    } else if (u < zs + ys) {
+        const unsigned uu = (unsigned)(u - zs), rows = G2 * px;
+        const unsigned k = uu / rows, r = uu - k * rows, jj = r / px;
+        ip = (int)(r - jj * px);
+        jp = jj < GHOST ? (int)jj : g.ny + (int)jj;
+        kp = (int)k + GHOST;
+    } else {
+        const unsigned uu = (unsigned)(u - zs - ys), jk = uu / G2, ii = uu - jk * G2;
+        const unsigned k = jk / (unsigned)g.ny, j = jk - k * (unsigned)g.ny;
+        ip = ii < GHOST ? (int)ii : g.nx + (int)ii;
+        jp = (int)j + GHOST;
+        kp = (int)k + GHOST;
     }
 }
 

@@ -8,9 +8,14 @@
 
 namespace hk {
 
+// one thread per ghost cell
 __global__ void k_halo(double *__restrict__ Q, Geo g)
 {
-    halo_item(Q, g, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= ghost_count(g)) return;
+    int ip, jp, kp;
+    ghost_cell(g, u, ip, jp, kp);
+    halo_cell(Q, g, ip, jp, kp);
 }
 
 // one thread per cell of the reconstruction box; the block's records are
@@ -222,7 +227,7 @@ static int sm_count()
 
 void launch_halo(double *Q, const Geo &g, cudaStream_t s)
 {
-    k_halo<<<blocks_for(g.pstride, 256), 256, 0, s>>>(Q, g);
+    k_halo<<<blocks_for(g.pstride - (long long)g.nx * g.ny * g.nz, 256), 256, 0, s>>>(Q, g);
 }
 
 template <typename R>
