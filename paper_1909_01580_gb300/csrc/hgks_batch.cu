@@ -276,6 +276,7 @@ static Geo make_geo(const hgks_grid_t *grid, double hx, const int bc[6])
     g.ncell = (long long)g.nx * g.ny * g.nz;
     g.h = hx;
     g.inv_h = 1.0 / hx;
+    hk::geo_divisors(g);
     for (int i = 0; i < 6; ++i) g.bc[i] = bc[i];
     return g;
 }

@@ -115,6 +115,24 @@ template <> HK_HD FluxK<float> fluxk<float>(const Scheme &S) { return S.kf; }
 // with the big stencil S' of Sec. 2) and one ghost layer in the
 // reconstruction arrays.
 constexpr int GHOST = 3;
+// Division by an invariant d >= 1 as a multiplication (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994,
+// the round-up method): with l = ceil(log2 d) and m = ceil(2^(31+l) / d),
+// floor(n / d) = floor(m n / 2^(31+l)) for every 0 <= n < 2^31 (m d - 2^(31+l)
+// < d <= 2^l); m < 2^32 for d <= 2^31.
+struct Div32 {
+    unsigned m;
+    int s;
+};
+HK_HD Div32 div32_of(unsigned d)
+{
+    int l = 0;
+    while (l < 31 && (1u << l) < d) ++l;
+    const unsigned long long p = 1ull << (31 + l);
+    return Div32{(unsigned)((p + d - 1) / d), 31 + l};
+}
+HK_HD unsigned div32(unsigned n, Div32 v) { return (unsigned)(((unsigned long long)v.m * n) >> v.s); }
+
 struct Geo {
     int nx, ny, nz;          // interior cells
     int px, py, pz;          // padded state extents (n + 2 GHOST)
@@ -124,7 +142,17 @@ struct Geo {
     long long ncell;         // nx*ny*nz
     double h, inv_h;         // cell edge and its inverse
     int bc[6];               // per face: 0 periodic, 1 reflective, 2 outflow
+    Div32 dv[4];             // division by nx, nx + 1, ny, ny + 1 (face index decode)
 };
+
+// the divisors of a Geo whose extents are set
+inline void geo_divisors(Geo &g)
+{
+    g.dv[0] = div32_of((unsigned)g.nx);
+    g.dv[1] = div32_of((unsigned)g.nx + 1u);
+    g.dv[2] = div32_of((unsigned)g.ny);
+    g.dv[3] = div32_of((unsigned)g.ny + 1u);
+}
 
 HK_HD long long pidx(const Geo &g, int i, int j, int k)
 {

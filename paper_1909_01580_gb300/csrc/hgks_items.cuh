@@ -668,9 +668,16 @@ __device__ __forceinline__ void flux_item(const R *__restrict__ coef, double *__
     const int gp = (int)(t & 3);
     const bool valid = face < nface && t < tlimit;
     if (!valid) face = nface - 1;
-    // (i, j, k) is the right cell; the left cell is one step back along D
+    // (i, j, k) is the right cell; the left cell is one step back along D;
+    // the face index decoded with the precomputed divisors of ex and ey
     int i, j, k;
-    split3(face, ex, ey, i, j, k);
+    {
+        const unsigned u = (unsigned)face;
+        const unsigned r = div32(u, g.dv[D == 0 ? 1 : 0]);
+        i = (int)(u - r * (unsigned)ex);
+        k = (int)div32(r, g.dv[D == 1 ? 3 : 2]);
+        j = (int)(r - (unsigned)k * (unsigned)ey);
+    }
     const int il = i - (D == 0), jl = j - (D == 1), kl = k - (D == 2);
     const R xa = (gp & 2) ? R(GAUSS_S) : R(-GAUSS_S);
     const R xb = (gp & 1) ? R(GAUSS_S) : R(-GAUSS_S);

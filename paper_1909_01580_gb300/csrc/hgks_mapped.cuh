@@ -1127,7 +1127,14 @@ __device__ __forceinline__ void flux_mapped_item(const R *__restrict__ coef, dou
     const bool valid = face < nface;
     if (!valid) face = nface - 1;
     int i, j, k;
-    split3(face, ex, ey, i, j, k);
+    {
+        // the face index decoded with the precomputed divisors of ex and ey
+        const unsigned u = (unsigned)face;
+        const unsigned r = div32(u, g.dv[D == 0 ? 1 : 0]);
+        i = (int)(u - r * (unsigned)ex);
+        k = (int)div32(r, g.dv[D == 1 ? 3 : 2]);
+        j = (int)(r - (unsigned)k * (unsigned)ey);
+    }
     const int il = i - (D == 0), jl = j - (D == 1), kl = k - (D == 2);
     constexpr int A = (D + 1) % 3, B = (D + 2) % 3;
     const R ea = (gp & 2) ? R(GAUSS_S) : R(-GAUSS_S), eb = (gp & 1) ? R(GAUSS_S) : R(-GAUSS_S);

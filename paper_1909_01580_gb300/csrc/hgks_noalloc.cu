@@ -120,6 +120,7 @@ extern "C" int hgks_flux_noalloc(const hgks_grid_t *grid, double gamma, double m
     g.ncell = (long long)g.nx * g.ny * g.nz;
     g.h = hx;
     g.inv_h = 1.0 / hx;
+    hk::geo_divisors(g);
     for (int i = 0; i < 6; ++i) g.bc[i] = bc[i];
     Scheme S;
     S.gamma = gamma;
