@@ -72,10 +72,20 @@ __global__ void __launch_bounds__(RM_BS, MapReconOcc<R>::blocks) k_recon_mapped(
                                                         R *__restrict__ coef, unsigned char *__restrict__ flag, Geo g,
                                                         MapGeo m, Scheme S, Ctl *ctl, int half)
 {
-    __shared__ R stage[RmStage<R>::n * RM_BS];
+    __shared__ __align__(16) R stage[RmStage<R>::n * RM_BS];
     if (!ctl->active) return;
-    recon_mapped_item<R>(Q, geo, coef, flag, g, m, ctl->mapS, S, ctl, stage + threadIdx.x,
-                         (long long)blockIdx.x * RM_BS + threadIdx.x);
+    const long long b = (long long)blockIdx.x * RM_BS;
+    recon_mapped_item<R>(Q, geo, coef, flag, g, m, ctl->mapS, S, ctl, stage + threadIdx.x, b + threadIdx.x);
+    if constexpr (RmStage<R>::dq) {
+        // FP32: the block's records, staged by the item, copied out with
+        // 16-byte coalesced stores
+        static_assert(RM_BS * MRec<R>::N <= RmStage<R>::n * RM_BS, "the records fit the stage");
+        __syncthreads();
+        const int nrec = (int)(g.cstride - b < RM_BS ? g.cstride - b : RM_BS);
+        const int4 *src = reinterpret_cast<const int4 *>(stage);
+        int4 *dst = reinterpret_cast<int4 *>(coef + b * MRec<R>::N);
+        for (int e = threadIdx.x; e < nrec * (MRec<R>::N * (int)sizeof(R) / 16); e += RM_BS) dst[e] = src[e];
+    }
 }
 
 // split state Q = Q_hi + Q_lo of the stage's Q for the mixed reconstruction

@@ -762,7 +762,15 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
                                                   const Geo &g, const MapGeo &m, double S, const Scheme &Sch, Ctl *ctl,
                                                   R *sh, long long t)
 {
-    if (t >= g.cstride) return;
+    // FP32: the records are staged in the block's shared memory for a
+    // coalesced copy (k_recon_mapped), so every thread takes part in the
+    // stage's barrier; a thread past the box reconstructs the last cell
+    // again and writes nothing
+    const bool valid = t < g.cstride;
+    if constexpr (!RmStage<R>::dq) {
+        if (!valid) return;
+    }
+    if (!valid) t = g.cstride - 1;
     int i, j, k;
     split3(t, g.cx, g.cy, i, j, k);
     i -= 1;
@@ -1008,6 +1016,14 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
         }
     }
     const R xmax = m_max(ext[0], m_max(ext[1], ext[2]));
+    // the cell's record: FP32 into its slot of the block's stage (the staged
+    // stencil data is no longer read once every thread is past this
+    // barrier), FP64 straight to global memory
+    R *rec = coef + t * MRec<R>::N;
+    if constexpr (fold) {
+        __syncthreads();
+        rec = (sh - threadIdx.x) + threadIdx.x * MRec<R>::N;
+    }
     R rad[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
@@ -1024,14 +1040,14 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
         }
 #pragma unroll
         for (int n = 10; n < MRec<R>::VS; ++n) out[n] = R(0);
-        store_mrec_part(coef + mrec_idx<R>(t, v, 0), out);
+        store_mrec_part(rec + MRec<R>::VS * (1 + v), out);
         // bound of |P_m - Q_c| at the Gauss points for all 25 P_m
         rad[v] = m_max(r0, bsum[v] * xmax) * R(1.0000001);
     }
     // a cell whose bound does not certify positivity is marked 2 and gets
     // the literal check in positivity_mapped_item (a kernel of its own, so
     // that its registers do not weigh on this one)
-    flag[t] = (Sch.limiter && !positivity_certain(qcv, rad, R(Sch.gamma))) ? 2 : 0;
+    if (valid) flag[t] = (Sch.limiter && !positivity_certain(qcv, rad, R(Sch.gamma))) ? 2 : 0;
     // the cell frame for the flux kernels
     {
         R fr[MRec<R>::VS];
@@ -1043,7 +1059,7 @@ __device__ __forceinline__ void recon_mapped_item(const double *__restrict__ Q, 
         for (int e = 0; e < 6; ++e) fr[4 + e] = Mh[e];
 #pragma unroll
         for (int n = 10; n < MRec<R>::VS; ++n) fr[n] = R(0);
-        store_mrec_part(coef + t * MRec<R>::N, fr);
+        store_mrec_part(rec, fr);
     }
 }
 
