@@ -38,12 +38,12 @@ UNIT = "cell-stage updates/s"
 # executed thread instructions of one ncu capture of the current build on a
 # TGV 64^3 x-face launch (smsp__sass_thread_inst_executed_op_{dfma,dadd,dmul,
 # ffma,fadd,fmul}_pred_on over its 1,064,960 Gauss points; 2 flop per FMA):
-#   FP64 path:  1063.2 DFMA + 127.5 DADD + 412.0 DMUL = 2666 flop, 1603 FP64 instructions
-#   mixed path: 984 FFMA + 115 FADD + 415 FMUL        = 2498 flop, 1514 FP32 instructions
+#   FP64 path:  1046.2 DFMA + 121.5 DADD + 411.0 DMUL = 2625 flop, 1579 FP64 instructions
+#   mixed path: 965 FFMA + 111 FADD + 414 FMUL        = 2455 flop, 1490 FP32 instructions
 # DRAM bytes per face (read + write) of one launch at 128^3 (inputs larger
 # than L2), from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum`.
-FLUX_FLOP_PER_GP = {"fp64": 2666.0, "mixed": 2498.0}
-FLUX_INST_PER_GP = {"fp64": 1603.0, "mixed": 1514.0}
+FLUX_FLOP_PER_GP = {"fp64": 2625.0, "mixed": 2455.0}
+FLUX_INST_PER_GP = {"fp64": 1579.0, "mixed": 1490.0}
 # x-face launch of TGV 128^3 (2,113,536 faces): FP64 855.05 MB read + 158.01 MB
 # written in 23.84 ms, mixed 511.24 MB + 151.65 MB in 0.501 ms (ncu, cold L2;
 # the mixed records carry 2 unused floats per variable: 240 B read per face)

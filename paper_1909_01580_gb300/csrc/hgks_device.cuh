@@ -456,19 +456,25 @@ template <int N, typename R> HK_HD void bapsi(const BMom<R> &B, const R c[5], R 
     o[4] = e;
 }
 
-// <u^n v' (c . psi') psi'> (T = 0) or <u^n w' (c . psi') psi'> (T = 1)
-template <int N, int T, typename R> HK_HD void bapsi_t(const BMom<R> &B, const R c[5], R o[5])
+// <u^n v' (c1 . psi') psi'> + <u^n w' (c2 . psi') psi'>: the tangential
+// terms of two slopes, which share their moment factors (v' and w' are
+// central, <v'^2> = <w'^2> = th, so only c1's v'-component and c2's
+// w'-component reach the mass and u-momentum, and the energy through Q)
+template <int N, typename R> HK_HD void bapsi_tt(const BMom<R> &B, const R c1[5], const R c2[5], R o[5])
 {
     const R *m = B.m;
-    const R ct = T ? c[3] : c[2];
+    const R ct = c1[2] + c2[3];
     const R tm0 = B.th * m[N], tm1 = B.th * m[N + 1], Q = bm_Q<N>(B);
     o[0] = ct * tm0;
     o[1] = ct * tm1;
-    R diag = c[0] * tm0;
-    diag += c[1] * tm1;
-    diag += c[4] * Q;
-    o[2] = T ? R(0) : diag;
-    o[3] = T ? diag : R(0);
+    R d = c1[0] * tm0;
+    d += c1[1] * tm1;
+    d += c1[4] * Q;
+    o[2] = d;
+    d = c2[0] * tm0;
+    d += c2[1] * tm1;
+    d += c2[4] * Q;
+    o[3] = d;
     o[4] = ct * Q;
 }
 
@@ -649,15 +655,16 @@ HK_HD void gks_flux(const R Wl[5], const R dWl[3][5], const R Wr[5], const R dWr
 #pragma unroll
         for (int k = 0; k < 5; ++k) Fa[k] += s.rho * t[k];
         {
-            // <u (u a_0 + v a_1 + w a_2) . psi psi> with v = V + v', w = W + w'
-            R t0[5], t1[5], t2[5], tv[5], tw[5];
-            bapsi<2>(B, a[0], t0);
-            bapsi<1>(B, a[1], t1);
-            bapsi<1>(B, a[2], t2);
-            bapsi_t<1, 0>(B, a[1], tv);
-            bapsi_t<1, 1>(B, a[2], tw);
+            // <u (u a_0 + v a_1 + w a_2) . psi psi> with v = V + v', w = W + w';
+            // the V and W parts as one slope V a_1 + W a_2 (bapsi is linear in it)
+            R cvw[5], t0[5], t1[5], tt[5];
 #pragma unroll
-            for (int k = 0; k < 5; ++k) t[k] = t0[k] + s.V * t1[k] + tv[k] + s.W * t2[k] + tw[k];
+            for (int k = 0; k < 5; ++k) cvw[k] = s.V * a[1][k] + s.W * a[2][k];
+            bapsi<2>(B, a[0], t0);
+            bapsi<1>(B, cvw, t1);
+            bapsi_tt<1>(B, a[1], a[2], tt);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) t[k] = t0[k] + t1[k] + tt[k];
             boost_out(s.V, s.W, t);
 #pragma unroll
             for (int k = 0; k < 5; ++k) Fb[k] += s.rho * t[k];
@@ -668,12 +675,11 @@ HK_HD void gks_flux(const R Wl[5], const R dWl[3][5], const R Wr[5], const R dWr
         for (int k = 0; k < 5; ++k) Fc[k] += s.rho * t[k];
         if (prfix) {
             // sum_i <u_i (a_i . psi) psi> and <(A . psi) psi> on this half line
-            R t0[5], tv[5], tw[5];
+            R t0[5], tt[5];
             bapsi<1>(B, a[0], t0);
-            bapsi_t<0, 0>(B, a[1], tv);
-            bapsi_t<0, 1>(B, a[2], tw);
+            bapsi_tt<0>(B, a[1], a[2], tt);
 #pragma unroll
-            for (int k = 0; k < 5; ++k) t[k] = t0[k] + s.V * d1[k] + tv[k] + s.W * d2[k] + tw[k];
+            for (int k = 0; k < 5; ++k) t[k] = t0[k] + s.V * d1[k] + s.W * d2[k] + tt[k];
             boost_out(s.V, s.W, t);
 #pragma unroll
             for (int k = 0; k < 5; ++k) Sb[k] += s.rho * t[k];
@@ -718,14 +724,14 @@ HK_HD void gks_flux(const R Wl[5], const R dWl[3][5], const R Wr[5], const R dWr
     bpsi<1>(B0, F0a);
     boost_out(s0.V, s0.W, F0a);
     {
-        R t0[5], t1[5], t2[5], tv[5], tw[5];
-        bapsi<2>(B0, abar[0], t0);
-        bapsi<1>(B0, abar[1], t1);
-        bapsi<1>(B0, abar[2], t2);
-        bapsi_t<1, 0>(B0, abar[1], tv);
-        bapsi_t<1, 1>(B0, abar[2], tw);
+        R cvw[5], t0[5], t1[5], tt[5];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) F0b[k] = t0[k] + s0.V * t1[k] + tv[k] + s0.W * t2[k] + tw[k];
+        for (int k = 0; k < 5; ++k) cvw[k] = s0.V * abar[1][k] + s0.W * abar[2][k];
+        bapsi<2>(B0, abar[0], t0);
+        bapsi<1>(B0, cvw, t1);
+        bapsi_tt<1>(B0, abar[1], abar[2], tt);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) F0b[k] = t0[k] + t1[k] + tt[k];
         boost_out(s0.V, s0.W, F0b);
     }
     bapsi<1>(B0, Abar, F0c);
