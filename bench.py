@@ -44,11 +44,11 @@ UNIT = "cell-stage updates/s"
 # than L2), from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum`.
 FLUX_FLOP_PER_GP = {"fp64": 2625.0, "mixed": 2455.0}
 FLUX_INST_PER_GP = {"fp64": 1579.0, "mixed": 1490.0}
-# x-face launch of TGV 128^3 (2,113,536 faces): FP64 855.05 MB read + 158.01 MB
-# written in 23.84 ms, mixed 511.24 MB + 151.65 MB in 0.501 ms (ncu, cold L2;
+# x-face launch of TGV 128^3 (2,113,536 faces): FP64 854.36 MB read + 157.89 MB
+# written in 23.48 ms, mixed 511.24 MB + 151.72 MB in 0.492 ms (ncu, cold L2;
 # the mixed records carry 2 unused floats per variable: 240 B read per face)
-FLUX_TRAFFIC_BYTES_PER_FACE = {"fp64": (855046912 + 158006528) / 2113536,
-                               "mixed": (511244032 + 151653120) / 2113536}
+FLUX_TRAFFIC_BYTES_PER_FACE = {"fp64": (854355200 + 157892608) / 2113536,
+                               "mixed": (511244288 + 151715072) / 2113536}
 # the algorithmic bytes per face: the two cells' reconstruction records
 # (Q_c and 9 coefficients of 5 variables) read once per face pair of a
 # cell, i.e. one record per face, and the face's 10 FP64 sums written once
